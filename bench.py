@@ -1,0 +1,304 @@
+#!/usr/bin/env python3
+"""Throughput of the messenger Gibbs sweep on GB300.
+
+Workload (default): the 256^3 batched-FP32 configuration — one Gaussian mock
+data set (L = 1000, P(k) = A k/(1+(k/0.02)^2)^2, radial selection, N = 0.1/R),
+64 linear k-shells, 16 independent chains swept together.  A step is one full
+sweep of all 16 chains: pass YZ (inverse y/z FFTs, messenger draw, forward z/y
+FFTs), pass X (forward x FFT, signal draw, shell sums, inverse x FFT) and the
+shell draw of P.  The chain state (1.08 GB) is larger than L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (under torchrun) each rank sweeps its own 16 chains (disjoint
+chain ids: replicas, no data-path collective); the time is the max over ranks.
+--impl reference times the FP64 CPU oracle on this host on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import mockgen  # noqa: E402
+from paper_1402_1763_gb300 import replicas  # noqa: E402
+
+METRIC = "Gibbs sweeps/s and voxel-updates/s at 256^3 (batched FP32 vs plain FP64); HBM %"
+UNIT = "voxel-updates/s"
+N_GRID = 256
+N_CHAINS = 16
+N_BINS = 64
+SEED = 3
+WORKLOAD = "gaussian-mock-256^3-fp32-16chains-64shells"
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(n: int, chains: int, esz: int):
+    """Bytes one launch of each pass must move ('Algorithmic bytes').
+
+    State per chain: n*n*(n/2) + n*n complex values, each pass reads and writes
+    it once.  The messenger constants (b, c) are one complex value per voxel,
+    read once per pass-YZ launch and shared by every chain of the data set.
+    """
+    cplx = 2 * esz
+    state = (n * n * (n // 2) + n * n) * cplx
+    yz = chains * 2 * state + n ** 3 * cplx
+    x = chains * 2 * state
+    return yz, x
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def run_reference(args, rank):
+    """FP64 CPU oracle on this host: each step is one sweep of one chain of the
+    same 256^3 workload (a bounded sample of the 16-chain step)."""
+    if rank != 0:
+        return 0
+    from oracle import sampler
+    m = mockgen.make_mock(N_GRID, seed=SEED, n_bins=N_BINS)
+    prob = sampler.make_problem(m.shape, m.L, m.N, m.R, m.d, N_BINS)
+    ch = sampler.Chains(prob, seed=SEED, chain_ids=[0])
+    for _ in range(args.warmup):
+        ch.sweep(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ch.sweep(1)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = N_GRID ** 3 / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "1 chain x 1 sweep per step (of 16 chains)",
+                       "grid": N_GRID, "shells": N_BINS},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "1 chain x 1 sweep of the 256^3 workload per step; numpy FP64, "
+                                       "single-threaded"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline(seconds_budget=25.0):
+    """The oracle as it stands, one chain of the workload, single-threaded numpy."""
+    from oracle import sampler
+    m = mockgen.make_mock(N_GRID, seed=SEED, n_bins=N_BINS)
+    prob = sampler.make_problem(m.shape, m.L, m.N, m.R, m.d, N_BINS)
+    ch = sampler.Chains(prob, seed=SEED, chain_ids=[0])
+    t0 = time.perf_counter()
+    sweeps = 0
+    while sweeps < 1 or (time.perf_counter() - t0 < seconds_budget / 3 and sweeps < 3):
+        ch.sweep(1)
+        sweeps += 1
+    dt = (time.perf_counter() - t0) / sweeps
+    return {"value": N_GRID ** 3 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sweeps} sweep(s) of 1 chain of the 256^3 workload (of 16 per step); "
+                      "numpy FP64 single-threaded"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local_rank = replicas.rank_world()
+
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1402_1763_gb300 import Sampler
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dd = dist if world > 1 else None
+    stream = torch.cuda.Stream()  # a real stream: the library enqueues on it, the events time it
+    torch.cuda.set_stream(stream)
+
+    m = mockgen.make_mock(N_GRID, seed=SEED, n_bins=N_BINS)
+    M = N_GRID ** 3
+    t_init = time.perf_counter()
+    smp = Sampler.single(N_GRID, m.L, m.N, m.R, m.d, N_BINS, SEED, precision=32, n_chains=N_CHAINS,
+                         chain_id0=replicas.chain_id_base(rank, N_CHAINS), stream=stream.cuda_stream)
+    init_s = time.perf_counter() - t_init
+
+    smp.sweep(args.warmup)
+    smp.sync()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    replicas.barrier(dd)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    smp.sweep(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    replicas.barrier(dd)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = replicas.max_over_ranks(ms, dd)
+    units_per_step = world * N_CHAINS * M
+    value = units_per_step / (ms * 1e-3)
+
+    # per-pass breakdown over the same number of sweeps (CUDA events per pass)
+    per = smp.sweep_timed(args.steps) / args.steps
+    yz_bytes, x_bytes = algorithmic_bytes(N_GRID, N_CHAINS, 4)
+    peak, peak_kind = measured_peaks()
+    kern = {"pass_yz": (per[0], yz_bytes), "pass_x": (per[1], x_bytes)}
+    dom = max(kern, key=lambda k: kern[k][0])
+    dom_ms, dom_bytes = kern[dom]
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    sweep_bytes = yz_bytes + x_bytes
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            tr = json.load(f)
+        traffic = tr.get(dom)
+
+    # end to end through the public API with host buffers: each step sweeps
+    # all chains and reads every chain's P(k) back to pinned host memory
+    from paper_1402_1763_gb300 import mg_read_pk
+    pk = [torch.empty(N_BINS + 1, dtype=torch.float64, pin_memory=True).numpy() for _ in range(N_CHAINS)]
+    smp.sync()
+    replicas.barrier(dd)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        smp.sweep(1)
+        for c in range(N_CHAINS):
+            mg_read_pk(smp.ctx, c, pk[c])
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = replicas.max_over_ranks(e2e_s, dd)
+    smp.close()
+
+    # the plain FP64 single-chain sampler on the same data, same GPU
+    fp64 = None
+    if rank == 0:
+        s64 = Sampler.single(N_GRID, m.L, m.N, m.R, m.d, N_BINS, SEED, precision=64, n_chains=1,
+                             stream=stream.cuda_stream)
+        s64.sweep(3)
+        s64.sync()
+        k64 = 10
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        s64.sweep(k64)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a0.elapsed_time(a1) / k64
+        s64.close()
+        fp64 = {"value": M / (ms64 * 1e-3), "unit": UNIT, "ms_per_sweep": ms64,
+                "config": "plain FP64, 1 chain, same 256^3 data"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": N_GRID, "chains_per_gpu": N_CHAINS, "shells": N_BINS,
+                   "precision": "FP32 FFTs and draws, FP64 shell sums and inverse-gamma parameters",
+                   "l2": "inputs larger than L2 (1.08 GB chain state per GPU)",
+                   "parallelism": f"replicas x{world}"},
+        "sweeps_per_s": 1e3 / ms,
+        "chain_sweeps_per_s": world * N_CHAINS * 1e3 / ms,
+        "fp64_single_chain": fp64,
+        "batched_fp32_over_fp64": (value / world) / fp64["value"] if fp64 else None,
+        "per_pass_ms": {"pass_yz": per[0], "pass_x": per[1], "shell_draw": per[2]},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": dom_bytes},
+        "sweep_roofline": {"algorithmic_bytes_per_step": sweep_bytes,
+                           "achieved_gbs": sweep_bytes / (ms * 1e-3) / 1e9,
+                           "frac": sweep_bytes / (ms * 1e-3) / 1e9 / peak},
+        "e2e": {"value": units_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": N_CHAINS * (N_BINS + 1) * 8},
+        "init_seconds": init_s,
+        "gpu_launches": args.steps * 3,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * mg.h — C ABI of the GB300 messenger Gibbs sampler.
+ *
+ * The library samples the joint posterior Pi(s, P(k) | d) of a Gaussian signal
+ * s on a periodic 3D grid and its isotropic power spectrum P(k), for linear
+ * data d = R s + eps with diagonal response R and diagonal noise covariance N
+ * (Jasche & Lavaux 2014, "Matrix-free large scale Bayesian inference in
+ * cosmology", Sec. 2).  One sweep is:
+ *   t | s, d       messenger draw voxel by voxel (Sec. 3.1, Alg. 1 first loop)
+ *   t_hat          forward orthonormal transform (Alg. 1, "ONT")
+ *   s_hat | t_hat  signal draw mode by mode (Sec. 3.1, Alg. 1 second loop)
+ *   s              inverse transform (Alg. 1)
+ *   P | s          inverse-gamma draw per k-shell (Sec. 3.2, Alg. 2 on shells)
+ * with T = tau 1, tau = tau_scale * min over observed voxels of N_i / R_i^2 and
+ * N~ = N - R T R (Sec. 2).  All random draws are Philox4x32-10 keyed by the
+ * seed with counter (index, sweep, chain, stream); see mg_philox().
+ *
+ * Conventions shared by every call:
+ *   - Grids are cubic: nx = ny = nz = n with n in {8, 12, 16, 24, 32, 48, 64,
+ *     96, 128, 192, 256} and equal box sides L[0] = L[1] = L[2].  Voxel index
+ *     i = (ix*n + iy)*n + iz (z fastest); voxel i sits at ((i.)+1/2) L/n.
+ *   - The transform is unitary: s_hat = DFT(s)/sqrt(M), M = n^3, V = L^3, and
+ *     S_hat(k) = (M/V) P(shell(k)), S_hat(0) = 0.
+ *   - Shells: with k_edges == NULL, n_bins linear shells of width k_Nyq/n_bins
+ *     on [0, k_Nyq) (shell b holds b^2 (n/2)^2 <= n_bins^2 |m|^2 < (b+1)^2 (n/2)^2,
+ *     m the integer wavenumber); otherwise n_bins+1 strictly increasing edges
+ *     (in units of 2 pi / L * |m|).  Modes outside the edges form one extra
+ *     overflow shell with index n_bins.  1 <= n_bins <= 254.
+ *   - Ownership: every pointer argument is borrowed for the duration of the
+ *     call only; input arrays are copied, output buffers belong to the caller.
+ *     The context owns all device memory it allocates.
+ *   - Errors: every call returns an mg_status and never throws.  A device-side
+ *     fault (numeric, timeout) or a CUDA error becomes sticky on the context:
+ *     later calls return it until mg_destroy.  mg_last_error() explains it.
+ *   - Streams: work is enqueued on mg_options.cuda_stream (a cudaStream_t; NULL
+ *     = the library's own stream).  Calls that return host data synchronise it.
+ */
+#ifndef MG_H_
+#define MG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MG_OK = 0,
+  MG_EINVAL = 1,       /* invalid argument or input data                      */
+  MG_ENOMEM = 2,       /* device or host allocation failed                    */
+  MG_ECUDA = 3,        /* a CUDA runtime call failed                          */
+  MG_ETIMEOUT = 4,     /* a device-side wait ran out of its budget            */
+  MG_ENUMERIC = 5,     /* a shell draw met sigma_b <= 0, X_b <= 0 or non-finite
+                          values; that shell kept its previous P              */
+  MG_ESTATE = 6,       /* call not valid in the context's current state       */
+  MG_EUNSUPPORTED = 7  /* valid request this build does not implement         */
+} mg_status;
+
+typedef struct mg_ctx mg_ctx;
+
+/* Grid shape and box side lengths (cubic, see above). */
+typedef struct {
+  int32_t nx, ny, nz;
+  double L[3];
+} mg_grid;
+
+typedef struct {
+  int32_t precision;      /* 64: FP64 everywhere.  32: FFTs and per-voxel /
+                             per-mode draws in FP32; shell sums and the
+                             inverse-gamma parameters in FP64.  Default 64.   */
+  int32_t n_chains;       /* chains per data set (group), >= 1.  Default 1.  */
+  int32_t chain_id0;      /* chain id of a group's first chain (Philox counter
+                             word 2); chain c uses chain_id0 + c.  Default 0. */
+  double tau_scale;       /* in (0, 1]: tau = tau_scale * min N_i/R_i^2.     */
+  const double* P0;       /* n_bins+1 starting powers shared by all chains, or
+                             NULL for flat S_hat = 1 (P = V/M).               */
+  int32_t record_every;   /* >0: accumulate per-voxel mean/variance of s and a
+                             P(k) trace every record_every-th sweep; 0 = off. */
+  int32_t fix_P;          /* nonzero: hold P fixed (signal sampler only).     */
+  int64_t timeout_cycles; /* budget of device-side waits in clock cycles;
+                             0 = library default.                            */
+  void* cuda_stream;      /* cudaStream_t the context enqueues on, or NULL.   */
+  int32_t yz_cluster;     /* CTAs per x-plane in the y/z pass (1, 2 or 4) for
+                             every grid size; 0 = the tuned default.  Sizes
+                             the build does not provide give MG_EUNSUPPORTED.*/
+} mg_options;
+
+/* Chain statistics (mg_read_stats). Arrays are caller-owned with the sizes
+ * given; pass NULL to skip one. */
+typedef struct {
+  int64_t sweeps;         /* sweeps completed by the context                 */
+  int64_t records;        /* sweeps folded into mean/var and the P trace     */
+  double tau;             /* tau of the chain's group                        */
+  int32_t n_bins;         /* shells of the chain's group (excluding overflow)*/
+  int64_t* n_b;           /* [n_bins+1] full-grid modes per shell (out)       */
+  double* sigma_b;        /* [n_bins+1] last sweep's sum_k w_k |s_hat_k|^2    */
+  double* chi_b;          /* [n_bins+1] last sweep's chi-square draw X_b      */
+  double* mean;           /* [M] per-voxel posterior mean of s (out)          */
+  double* var;            /* [M] per-voxel posterior variance of s (out)      */
+} mg_stats;
+
+/* Fill *opt with the defaults listed in mg_options. */
+void mg_options_init(mg_options* opt);
+
+/* Create a context for one data set (Sec. 2 problem statement: grid, noise
+ * covariance N, response R, data d, k-shells, seed).  N, R, d: host arrays of
+ * M doubles.  R >= 0 (R = 0 marks an unobserved voxel); N > 0 wherever R > 0
+ * (ignored where R = 0); at least one voxel observed.  k_edges: NULL or
+ * n_bins+1 doubles.  The chains start at s = 0 and P = opt->P0.
+ * Errors: MG_EINVAL for invalid arguments or data, MG_EUNSUPPORTED for grids
+ * this build does not cover, MG_ENOMEM / MG_ECUDA.  *out is NULL on error. */
+mg_status mg_init(mg_ctx** out, const mg_grid* grid, const double* N, const double* R,
+                  const double* d, const double* k_edges, int32_t n_bins, uint64_t seed,
+                  const mg_options* opt);
+
+/* Create one context holding n_groups independent data sets of possibly
+ * different grid sizes, each with opt->n_chains chains; every sweep advances
+ * all chains (Sec. 3.4: independent chains need no communication).  Arrays
+ * are indexed by group; k_edges[g] may be NULL.  Chains are numbered group by
+ * group: chain = g * n_chains + c.  Errors as mg_init. */
+mg_status mg_init_batch(mg_ctx** out, int32_t n_groups, const mg_grid* grids,
+                        const double* const* N, const double* const* R, const double* const* d,
+                        const double* const* k_edges, const int32_t* n_bins,
+                        const uint64_t* seeds, const mg_options* opt);
+
+/* Run n_sweeps Gibbs sweeps (Sec. 3.2: Alg. 1 then Alg. 2) on every chain,
+ * asynchronously on the context's stream. n_sweeps >= 0. */
+mg_status mg_sweep(mg_ctx* ctx, int64_t n_sweeps);
+
+/* Like mg_sweep, but launches the passes one by one (no CUDA graph) with
+ * CUDA events around each, and adds the elapsed milliseconds of all sweeps to
+ * ms_out[0] (pass YZ: inverse y/z transforms, messenger draw, forward z/y),
+ * ms_out[1] (pass X: forward x transform, signal draw, shell sums, inverse x)
+ * and ms_out[2] (shell draw of P).  Synchronises. */
+mg_status mg_sweep_timed(mg_ctx* ctx, int64_t n_sweeps, double* ms_out);
+
+/* Current signal s of one chain in real space: M values of the context's
+ * precision (double for 64, float for 32), written to out — device memory if
+ * out_is_device, else host memory (the call then synchronises). */
+mg_status mg_read_s(mg_ctx* ctx, int32_t chain, void* out, int32_t out_is_device);
+
+/* Current P of one chain: n_bins+1 doubles to host memory, the last one the
+ * overflow shell.  Synchronises. */
+mg_status mg_read_pk(mg_ctx* ctx, int32_t chain, double* out);
+
+/* Statistics of one chain (see mg_stats). Synchronises. */
+mg_status mg_read_stats(mg_ctx* ctx, int32_t chain, mg_stats* out);
+
+/* Replace one chain's signal (M values of the context's precision, host or
+ * device) — for over-dispersed starts and checkpoint resume. */
+mg_status mg_set_s(mg_ctx* ctx, int32_t chain, const void* s, int32_t s_is_device);
+
+/* Replace one chain's P (n_bins+1 host doubles, all > 0). */
+mg_status mg_set_pk(mg_ctx* ctx, int32_t chain, const double* P);
+
+/* Sweep counter (Philox counter word 1 of the next sweep); mg_set_sweep_count
+ * restores it when resuming from a checkpoint. */
+mg_status mg_get_sweep_count(mg_ctx* ctx, int64_t* out);
+mg_status mg_set_sweep_count(mg_ctx* ctx, int64_t sweeps);
+
+/* Shape queries: total chains, grid size n and shell count of one chain. */
+mg_status mg_chain_info(mg_ctx* ctx, int32_t chain, int32_t* n, int32_t* n_bins, int32_t* n_chains);
+
+/* Wait for all enqueued work and report any sticky device status. */
+mg_status mg_sync(mg_ctx* ctx);
+
+/* Human-readable description of the last error on ctx (never NULL). */
+const char* mg_last_error(const mg_ctx* ctx);
+
+/* Free everything the context owns; ctx may be NULL. */
+void mg_destroy(mg_ctx* ctx);
+
+/* Raw Philox4x32-10 words on the device (Salmon et al. 2011; the per-core
+ * generators of Sec. 3.4): for i in [0, n_calls), call i uses counter
+ * (ctr0 + i, ctr1, ctr2, ctr3) and key (seed & 0xffffffff, seed >> 32) and
+ * writes its 4 words to out_device[4i .. 4i+3].  out_device: device memory of
+ * 4*n_calls uint32.  stream: cudaStream_t or NULL.  Synchronises. */
+mg_status mg_philox(uint64_t seed, uint32_t ctr0, uint32_t ctr1, uint32_t ctr2, uint32_t ctr3,
+                    int64_t n_calls, uint32_t* out_device, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MG_H_ */

@@ -1,0 +1,852 @@
+// Host side of the C ABI declared in include/mg.h: context set-up, the sweep
+// schedule (pass YZ, pass X, shell draw per sweep; captured into a CUDA graph),
+// reads and writes of chain state, and error handling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_aux.cuh"
+#include "mg_launch.h"
+
+using namespace mg;
+
+namespace {
+
+constexpr int kMaxBins = 254;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+struct Group {
+  int n = 0;
+  double L = 0;
+  int B = 0;
+  uint64_t seed = 0;
+  double tau = 0;
+  size_t M = 0;
+  std::vector<long long> n_b;  // B+1
+  std::shared_ptr<DevBuf> bc, bin_of_m2, n_b_dev;
+};
+
+struct Chain {
+  int group = 0;
+  uint32_t chain_id = 0;
+  std::shared_ptr<DevBuf> main, nyq, coef, partial, P, sig, chi, mean, m2;
+};
+
+// All chains of one grid size are launched together.
+struct SizeClass {
+  int n = 0;
+  int C = 1;
+  int B_max = 0;
+  std::vector<int> chains;         // context chain indices
+  std::shared_ptr<DevBuf> d_desc;  // ChainDev<T>[chains.size()]
+  std::shared_ptr<DevBuf> tw;      // W_n^k, k < n, in the context precision
+};
+
+}  // namespace
+
+struct mg_ctx {
+  int precision = 64;
+  int fix_P = 0;
+  int record_every = 0;
+  long long records = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<Group> groups;
+  std::vector<Chain> chains;
+  std::vector<SizeClass> classes;
+  std::shared_ptr<DevBuf> d_draw;  // DrawDev[chains]
+  std::shared_ptr<DevBuf> d_sweep, d_status, d_scratch_s;
+  int B_max = 0;
+  long long sweeps = 0;
+  mg_status sticky = MG_OK;
+  std::string err;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_failed = false;
+};
+
+namespace {
+
+mg_status fail(mg_ctx* c, mg_status s, const std::string& msg) {
+  if (c) {
+    c->err = msg;
+    if (s == MG_ECUDA || s == MG_ENUMERIC || s == MG_ETIMEOUT) c->sticky = s;
+  }
+  return s;
+}
+
+#define MG_CUDA(ctx, call)                                                        \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return fail(ctx, MG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+std::shared_ptr<DevBuf> dalloc(size_t bytes, cudaError_t* err) {
+  auto b = std::make_shared<DevBuf>();
+  b->bytes = bytes;
+  *err = cudaMalloc(&b->p, bytes ? bytes : 16);
+  if (*err != cudaSuccess) b->p = nullptr;
+  return b;
+}
+
+bool is_supported_n(int n) {
+  static const int ok[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256};
+  for (int v : ok)
+    if (v == n) return true;
+  return false;
+}
+
+// Shell id of every |m|^2 (host, once per group).  Linear edges use the exact
+// integer test b^2 (n/2)^2 <= B^2 m^2 (ties go to the upper shell); explicit
+// edges compare |k| = (2 pi / L) sqrt(m^2) in FP64.  Out-of-range -> B.
+std::vector<uint8_t> build_bin_table(int n, double L, int B, const double* edges, std::vector<long long>* n_b) {
+  const int h = n / 2;
+  const int max_m2 = 3 * h * h;
+  std::vector<uint8_t> tab(size_t(max_m2) + 1, uint8_t(B));
+  for (int m2 = 1; m2 <= max_m2; ++m2) {
+    int b;
+    if (!edges) {
+      // largest b with b^2 h^2 <= B^2 m2: b = floor(sqrt(B^2 m2) / h), exact
+      const unsigned long long t = (unsigned long long)B * B * (unsigned long long)m2;
+      unsigned long long q = (unsigned long long)std::sqrt((double)t);
+      while (q * q > t) --q;
+      while ((q + 1) * (q + 1) <= t) ++q;
+      b = int(q / (unsigned long long)h);
+      if (b >= B) b = B;
+    } else {
+      const double k = 2.0 * M_PI / L * std::sqrt(double(m2));
+      b = -1;
+      for (int e = 0; e < B; ++e)
+        if (k >= edges[e]) b = e;
+      if (b < 0 || k >= edges[B]) b = B;
+    }
+    tab[m2] = uint8_t(b);
+  }
+  // full-grid mode counts per shell
+  n_b->assign(B + 1, 0);
+  std::vector<long long> cnt(size_t(max_m2) + 1, 0);
+  std::vector<int> m2_of(n);
+  for (int k = 0; k < n; ++k) {
+    const int m = k <= h ? k : k - n;
+    m2_of[k] = m * m;
+  }
+  for (int a = 0; a < n; ++a)
+    for (int b2 = 0; b2 < n; ++b2)
+      for (int c = 0; c < n; ++c) ++cnt[m2_of[a] + m2_of[b2] + m2_of[c]];
+  for (int m2 = 1; m2 <= max_m2; ++m2) (*n_b)[tab[m2]] += cnt[m2];
+  return tab;
+}
+
+template <typename T>
+std::vector<typename VT<T>::c2> twiddles(int n) {
+  std::vector<typename VT<T>::c2> t(n);
+  for (int k = 0; k < n; ++k) {
+    const long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)k / (long double)n;
+    t[k].x = T(std::cos(a));
+    t[k].y = T(std::sin(a));
+  }
+  return t;
+}
+
+template <typename T>
+mg_status upload_descriptors(mg_ctx* c) {
+  using V2 = typename VT<T>::c2;
+  for (auto& sc : c->classes) {
+    std::vector<ChainDev<T>> h(sc.chains.size());
+    for (size_t i = 0; i < sc.chains.size(); ++i) {
+      const Chain& ch = c->chains[sc.chains[i]];
+      const Group& g = c->groups[ch.group];
+      ChainDev<T>& d = h[i];
+      d.main = static_cast<V2*>(ch.main->p);
+      d.nyq = static_cast<V2*>(ch.nyq->p);
+      d.bc = static_cast<const V2*>(g.bc->p);
+      d.coef = static_cast<const V2*>(ch.coef->p);
+      d.partial = static_cast<double*>(ch.partial->p);
+      d.bin_of_m2 = static_cast<const uint8_t*>(g.bin_of_m2->p);
+      d.s_out = nullptr;
+      d.s_in = nullptr;
+      d.tau = T(g.tau);
+      d.k0 = uint32_t(g.seed & 0xffffffffu);
+      d.k1 = uint32_t(g.seed >> 32);
+      d.chain_id = ch.chain_id;
+      d.B = g.B;
+    }
+    cudaError_t e;
+    sc.d_desc = dalloc(h.size() * sizeof(ChainDev<T>), &e);
+    MG_CUDA(c, e);
+    MG_CUDA(c, cudaMemcpy(sc.d_desc->p, h.data(), h.size() * sizeof(ChainDev<T>), cudaMemcpyHostToDevice));
+    const auto tw = twiddles<T>(sc.n);
+    sc.tw = dalloc(tw.size() * sizeof(V2), &e);
+    MG_CUDA(c, e);
+    MG_CUDA(c, cudaMemcpy(sc.tw->p, tw.data(), tw.size() * sizeof(V2), cudaMemcpyHostToDevice));
+  }
+  std::vector<DrawDev> dd(c->chains.size());
+  for (size_t i = 0; i < c->chains.size(); ++i) {
+    const Chain& ch = c->chains[i];
+    const Group& g = c->groups[ch.group];
+    DrawDev& d = dd[i];
+    d.partial = static_cast<const double*>(ch.partial->p);
+    d.n_tiles = pass_x_tiles(g.n);
+    d.B = g.B;
+    d.n_b = static_cast<const long long*>(g.n_b_dev->p);
+    d.P = static_cast<double*>(ch.P->p);
+    d.sig_last = static_cast<double*>(ch.sig->p);
+    d.chi_last = static_cast<double*>(ch.chi->p);
+    d.coef = ch.coef->p;
+    d.tau = g.tau;
+    d.M = double(g.M);
+    d.V = g.L * g.L * g.L;
+  }
+  cudaError_t e;
+  c->d_draw = dalloc(dd.size() * sizeof(DrawDev), &e);
+  MG_CUDA(c, e);
+  MG_CUDA(c, cudaMemcpy(c->d_draw->p, dd.data(), dd.size() * sizeof(DrawDev), cudaMemcpyHostToDevice));
+  return MG_OK;
+}
+
+template <typename T>
+mg_status launch_shell_draw(mg_ctx* c, int draw, bool count_sweep) {
+  const dim3 grid(unsigned(c->chains.size()), unsigned(c->B_max + 1));
+  shell_draw_kernel<T><<<grid, 256, 0, c->stream>>>(static_cast<const DrawDev*>(c->d_draw->p), draw, c->fix_P,
+                                                    static_cast<int*>(c->d_status->p),
+                                                    count_sweep ? static_cast<uint32_t*>(c->d_sweep->p) : nullptr);
+  MG_CUDA(c, cudaGetLastError());
+  return MG_OK;
+}
+
+// which: bit 1 = pass YZ of every size class, bit 2 = pass X, bit 4 = shell draw.
+template <typename T>
+mg_status enqueue_passes(mg_ctx* c, int which) {
+  const uint32_t* sw = static_cast<const uint32_t*>(c->d_sweep->p);
+  if (which & 1) {
+    for (auto& sc : c->classes) {
+      MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, 0, static_cast<const ChainDev<T>*>(sc.d_desc->p),
+                                   int(sc.chains.size()), sw, sc.tw->p, c->stream));
+    }
+  }
+  if (which & 2) {
+    for (auto& sc : c->classes) {
+      MG_CUDA(c, launch_pass_x<T>(sc.n, static_cast<const ChainDev<T>*>(sc.d_desc->p), int(sc.chains.size()), sw,
+                                  sc.tw->p, sc.B_max, c->stream));
+    }
+  }
+  if (which & 4) return launch_shell_draw<T>(c, 1, true);
+  return MG_OK;
+}
+
+mg_status enqueue_sweep(mg_ctx* c) {
+  return c->precision == 32 ? enqueue_passes<float>(c, 7) : enqueue_passes<double>(c, 7);
+}
+
+// One chain's descriptor with an input or output field pointer attached.
+template <typename T>
+mg_status single_chain_desc(mg_ctx* c, int chain, T* s_out, const T* s_in, SizeClass** sc_out,
+                            std::shared_ptr<DevBuf>* desc) {
+  for (auto& sc : c->classes) {
+    for (size_t i = 0; i < sc.chains.size(); ++i) {
+      if (sc.chains[i] != chain) continue;
+      ChainDev<T> h;
+      MG_CUDA(c, cudaMemcpy(&h, static_cast<ChainDev<T>*>(sc.d_desc->p) + i, sizeof(h), cudaMemcpyDeviceToHost));
+      h.s_out = s_out;
+      h.s_in = s_in;
+      cudaError_t e;
+      *desc = dalloc(sizeof(h), &e);
+      MG_CUDA(c, e);
+      MG_CUDA(c, cudaMemcpyAsync((*desc)->p, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+      MG_CUDA(c, cudaStreamSynchronize(c->stream));
+      *sc_out = &sc;
+      return MG_OK;
+    }
+  }
+  return fail(c, MG_EINVAL, "chain index out of range");
+}
+
+template <typename T>
+mg_status materialize(mg_ctx* c, int chain, T* out_dev) {
+  SizeClass* sc;
+  std::shared_ptr<DevBuf> desc;
+  mg_status s = single_chain_desc<T>(c, chain, out_dev, nullptr, &sc, &desc);
+  if (s != MG_OK) return s;
+  MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, 1, static_cast<const ChainDev<T>*>(desc->p), 1,
+                               static_cast<const uint32_t*>(c->d_sweep->p), sc->tw->p, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+template <typename T>
+mg_status load_s(mg_ctx* c, int chain, const T* in_dev) {
+  SizeClass* sc;
+  std::shared_ptr<DevBuf> desc;
+  mg_status s = single_chain_desc<T>(c, chain, nullptr, in_dev, &sc, &desc);
+  if (s != MG_OK) return s;
+  MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, 2, static_cast<const ChainDev<T>*>(desc->p), 1,
+                               static_cast<const uint32_t*>(c->d_sweep->p), sc->tw->p, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+mg_status check_status(mg_ctx* c) {
+  if (c->sticky != MG_OK) return c->sticky;
+  int st = 0;
+  MG_CUDA(c, cudaMemcpyAsync(&st, c->d_status->p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (st & kStTimeout) return fail(c, MG_ETIMEOUT, "a device-side wait ran out of its budget");
+  if (st & kStNumeric)
+    return fail(c, MG_ENUMERIC, "a shell draw met a non-positive or non-finite sum; the shell kept its P");
+  return MG_OK;
+}
+
+template <typename T>
+mg_status record_stats(mg_ctx* c) {
+  ++c->records;
+  const double inv = 1.0 / double(c->records);
+  for (size_t ci = 0; ci < c->chains.size(); ++ci) {
+    const Group& g = c->groups[c->chains[ci].group];
+    T* s = static_cast<T*>(c->d_scratch_s->p);
+    SizeClass* sc;
+    std::shared_ptr<DevBuf> desc;
+    mg_status st = single_chain_desc<T>(c, int(ci), s, nullptr, &sc, &desc);
+    if (st != MG_OK) return st;
+    MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, 1, static_cast<const ChainDev<T>*>(desc->p), 1,
+                                 static_cast<const uint32_t*>(c->d_sweep->p), sc->tw->p, c->stream));
+    welford_kernel<T><<<1024, 256, 0, c->stream>>>(s, static_cast<double*>(c->chains[ci].mean->p),
+                                                   static_cast<double*>(c->chains[ci].m2->p), g.M, inv);
+    MG_CUDA(c, cudaGetLastError());
+    MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return MG_OK;
+}
+
+mg_status validate_grid(const mg_grid* g) {
+  if (!g) return MG_EINVAL;
+  if (g->nx != g->ny || g->ny != g->nz) return MG_EUNSUPPORTED;
+  if (!(g->L[0] > 0) || g->L[0] != g->L[1] || g->L[1] != g->L[2] || !std::isfinite(g->L[0]))
+    return g->L[0] > 0 ? MG_EUNSUPPORTED : MG_EINVAL;
+  if (!is_supported_n(g->nx)) return MG_EUNSUPPORTED;
+  return MG_OK;
+}
+
+template <typename T>
+mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double* const* N, const double* const* R,
+                    const double* const* d, const double* const* k_edges, const int32_t* n_bins,
+                    const uint64_t* seeds, const mg_options* opt) {
+  using V2 = typename VT<T>::c2;
+  cudaError_t e;
+  c->d_sweep = dalloc(sizeof(uint32_t), &e);
+  MG_CUDA(c, e);
+  c->d_status = dalloc(sizeof(int), &e);
+  MG_CUDA(c, e);
+  MG_CUDA(c, cudaMemsetAsync(c->d_sweep->p, 0, sizeof(uint32_t), c->stream));
+  MG_CUDA(c, cudaMemsetAsync(c->d_status->p, 0, sizeof(int), c->stream));
+  size_t max_M = 0;
+  std::map<int, int> class_of_n;
+  for (int gi = 0; gi < n_groups; ++gi) {
+    const mg_grid& gr = grids[gi];
+    Group g;
+    g.n = gr.nx;
+    g.L = gr.L[0];
+    g.B = n_bins[gi];
+    g.seed = seeds[gi];
+    g.M = size_t(g.n) * g.n * g.n;
+    max_M = std::max(max_M, g.M);
+    const double* edges = k_edges ? k_edges[gi] : nullptr;
+    if (edges) {
+      for (int b = 0; b <= g.B; ++b)
+        if (!std::isfinite(edges[b]) || (b == 0 ? edges[0] < 0 : edges[b] <= edges[b - 1]))
+          return fail(c, MG_EINVAL, "k_edges must be finite, >= 0 and strictly increasing");
+    }
+    // inputs to the device, tau bound and validation
+    auto dN = dalloc(g.M * 8, &e);
+    MG_CUDA(c, e);
+    auto dR = dalloc(g.M * 8, &e);
+    MG_CUDA(c, e);
+    auto dd = dalloc(g.M * 8, &e);
+    MG_CUDA(c, e);
+    auto dmin = dalloc(2 * sizeof(unsigned long long), &e);
+    MG_CUDA(c, e);
+    MG_CUDA(c, cudaMemcpyAsync(dN->p, N[gi], g.M * 8, cudaMemcpyHostToDevice, c->stream));
+    MG_CUDA(c, cudaMemcpyAsync(dR->p, R[gi], g.M * 8, cudaMemcpyHostToDevice, c->stream));
+    MG_CUDA(c, cudaMemcpyAsync(dd->p, d[gi], g.M * 8, cudaMemcpyHostToDevice, c->stream));
+    unsigned long long init2[2] = {0x7FF0000000000000ull, 0ull};
+    MG_CUDA(c, cudaMemcpyAsync(dmin->p, init2, sizeof(init2), cudaMemcpyHostToDevice, c->stream));
+    MG_CUDA(c, cudaMemsetAsync(c->d_status->p, 0, sizeof(int), c->stream));
+    auto* mb = static_cast<unsigned long long*>(dmin->p);
+    tau_bound_kernel<<<1024, 256, 0, c->stream>>>(static_cast<const double*>(dN->p),
+                                                  static_cast<const double*>(dR->p),
+                                                  static_cast<const double*>(dd->p), g.M, mb, mb + 1,
+                                                  static_cast<int*>(c->d_status->p));
+    MG_CUDA(c, cudaGetLastError());
+    unsigned long long res[2];
+    int st = 0;
+    MG_CUDA(c, cudaMemcpyAsync(res, dmin->p, sizeof(res), cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(c, cudaMemcpyAsync(&st, c->d_status->p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (st & kStBadInput)
+      return fail(c, MG_EINVAL, "invalid data: need finite R >= 0, and N > 0 and finite d where R > 0");
+    if (res[1] == 0) return fail(c, MG_EINVAL, "no observed voxel (R > 0 nowhere)");
+    double bound;
+    std::memcpy(&bound, &res[0], sizeof(double));
+    g.tau = opt->tau_scale * bound;
+    MG_CUDA(c, cudaMemsetAsync(c->d_status->p, 0, sizeof(int), c->stream));
+    g.bc = dalloc(g.M * sizeof(V2), &e);
+    MG_CUDA(c, e);
+    messenger_constants_kernel<T><<<1024, 256, 0, c->stream>>>(
+        static_cast<const double*>(dN->p), static_cast<const double*>(dR->p), static_cast<const double*>(dd->p), g.M,
+        g.tau, static_cast<V2*>(g.bc->p));
+    MG_CUDA(c, cudaGetLastError());
+    // shells
+    const auto tab = build_bin_table(g.n, g.L, g.B, edges, &g.n_b);
+    g.bin_of_m2 = dalloc(tab.size(), &e);
+    MG_CUDA(c, e);
+    MG_CUDA(c, cudaMemcpy(g.bin_of_m2->p, tab.data(), tab.size(), cudaMemcpyHostToDevice));
+    g.n_b_dev = dalloc(g.n_b.size() * sizeof(long long), &e);
+    MG_CUDA(c, e);
+    MG_CUDA(c, cudaMemcpy(g.n_b_dev->p, g.n_b.data(), g.n_b.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    MG_CUDA(c, cudaStreamSynchronize(c->stream));  // dN, dR, dd freed below
+    c->B_max = std::max(c->B_max, g.B);
+    c->groups.push_back(std::move(g));
+    const Group& gg = c->groups.back();
+    // chains
+    if (!class_of_n.count(gg.n)) {
+      class_of_n[gg.n] = int(c->classes.size());
+      SizeClass sc;
+      sc.n = gg.n;
+      int choices[4];
+      const int nch = yz_cluster_choices(gg.n, c->precision, choices, 4);
+      sc.C = choices[0];
+      if (opt->yz_cluster) {
+        bool ok = false;
+        for (int k = 0; k < nch; ++k) ok = ok || choices[k] == opt->yz_cluster;
+        if (!ok) return fail(c, MG_EUNSUPPORTED, "yz_cluster not built for this grid size and precision");
+        sc.C = opt->yz_cluster;
+      }
+      c->classes.push_back(sc);
+    }
+    SizeClass& sc = c->classes[class_of_n[gg.n]];
+    sc.B_max = std::max(sc.B_max, gg.B);
+    const int H = gg.n / 2;
+    for (int k = 0; k < opt->n_chains; ++k) {
+      Chain ch;
+      ch.group = gi;
+      ch.chain_id = uint32_t(opt->chain_id0 + k);
+      const size_t main_b = size_t(gg.n) * gg.n * H * sizeof(V2), nyq_b = size_t(gg.n) * gg.n * sizeof(V2);
+      ch.main = dalloc(main_b, &e);
+      MG_CUDA(c, e);
+      ch.nyq = dalloc(nyq_b, &e);
+      MG_CUDA(c, e);
+      MG_CUDA(c, cudaMemsetAsync(ch.main->p, 0, main_b, c->stream));
+      MG_CUDA(c, cudaMemsetAsync(ch.nyq->p, 0, nyq_b, c->stream));
+      ch.coef = dalloc(size_t(gg.B + 2) * sizeof(V2), &e);
+      MG_CUDA(c, e);
+      ch.partial = dalloc(size_t(pass_x_tiles(gg.n)) * (gg.B + 1) * 2 * sizeof(double), &e);
+      MG_CUDA(c, e);
+      ch.P = dalloc(size_t(gg.B + 1) * sizeof(double), &e);
+      MG_CUDA(c, e);
+      ch.sig = dalloc(size_t(gg.B + 1) * sizeof(double), &e);
+      MG_CUDA(c, e);
+      ch.chi = dalloc(size_t(gg.B + 1) * sizeof(double), &e);
+      MG_CUDA(c, e);
+      MG_CUDA(c, cudaMemsetAsync(ch.sig->p, 0, size_t(gg.B + 1) * sizeof(double), c->stream));
+      MG_CUDA(c, cudaMemsetAsync(ch.chi->p, 0, size_t(gg.B + 1) * sizeof(double), c->stream));
+      std::vector<double> P0(gg.B + 1, (gg.L * gg.L * gg.L) / double(gg.M));
+      if (opt->P0)
+        for (int b = 0; b <= gg.B; ++b) P0[b] = opt->P0[b];
+      MG_CUDA(c, cudaMemcpy(ch.P->p, P0.data(), P0.size() * sizeof(double), cudaMemcpyHostToDevice));
+      if (c->record_every > 0) {
+        ch.mean = dalloc(gg.M * sizeof(double), &e);
+        MG_CUDA(c, e);
+        ch.m2 = dalloc(gg.M * sizeof(double), &e);
+        MG_CUDA(c, e);
+        MG_CUDA(c, cudaMemsetAsync(ch.mean->p, 0, gg.M * sizeof(double), c->stream));
+        MG_CUDA(c, cudaMemsetAsync(ch.m2->p, 0, gg.M * sizeof(double), c->stream));
+      }
+      c->classes[class_of_n[gg.n]].chains.push_back(int(c->chains.size()));
+      c->chains.push_back(std::move(ch));
+    }
+  }
+  if (c->record_every > 0) {
+    c->d_scratch_s = dalloc(max_M * sizeof(T), &e);
+    MG_CUDA(c, e);
+  }
+  mg_status s = upload_descriptors<T>(c);
+  if (s != MG_OK) return s;
+  for (auto& sc : c->classes) {
+    for (int mode = 0; mode < 3; ++mode)
+      MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, mode, nullptr, 0, nullptr, nullptr, c->stream));
+    MG_CUDA(c, launch_pass_x<T>(sc.n, nullptr, 0, nullptr, nullptr, sc.B_max, c->stream));
+  }
+  s = launch_shell_draw<T>(c, 0, false);
+  if (s != MG_OK) return s;
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+mg_status create(mg_ctx** out, int32_t n_groups, const mg_grid* grids, const double* const* N,
+                 const double* const* R, const double* const* d, const double* const* k_edges,
+                 const int32_t* n_bins, const uint64_t* seeds, const mg_options* opt_in) {
+  if (!out) return MG_EINVAL;
+  *out = nullptr;
+  if (n_groups < 1 || !grids || !N || !R || !d || !n_bins || !seeds) return MG_EINVAL;
+  mg_options opt;
+  mg_options_init(&opt);
+  if (opt_in) opt = *opt_in;
+  if (opt.precision != 32 && opt.precision != 64) return MG_EINVAL;
+  if (opt.n_chains < 1 || opt.chain_id0 < 0) return MG_EINVAL;
+  if (!(opt.tau_scale > 0.0 && opt.tau_scale <= 1.0)) return MG_EINVAL;
+  if (opt.record_every < 0) return MG_EINVAL;
+  if (opt.yz_cluster < 0) return MG_EINVAL;
+  for (int g = 0; g < n_groups; ++g) {
+    mg_status s = validate_grid(&grids[g]);
+    if (s != MG_OK) return s;
+    if (n_bins[g] < 1 || n_bins[g] > kMaxBins) return MG_EINVAL;
+    if (!N[g] || !R[g] || !d[g]) return MG_EINVAL;
+    if (opt.P0)
+      for (int b = 0; b <= n_bins[g]; ++b)
+        if (!(opt.P0[b] > 0.0) || !std::isfinite(opt.P0[b])) return MG_EINVAL;
+  }
+  if (opt.P0) {
+    for (int g = 1; g < n_groups; ++g)
+      if (n_bins[g] != n_bins[0]) return MG_EINVAL;  // one P0 shared by all groups
+  }
+  auto* c = new mg_ctx();
+  c->precision = opt.precision;
+  c->fix_P = opt.fix_P ? 1 : 0;
+  c->record_every = opt.record_every;
+  if (opt.cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(opt.cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return MG_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  const mg_status s = c->precision == 32
+                          ? init_impl<float>(c, n_groups, grids, N, R, d, k_edges, n_bins, seeds, &opt)
+                          : init_impl<double>(c, n_groups, grids, N, R, d, k_edges, n_bins, seeds, &opt);
+  if (s != MG_OK) {
+    mg_destroy(c);
+    return s;
+  }
+  *out = c;
+  return MG_OK;
+}
+
+bool valid_chain(const mg_ctx* c, int32_t chain) { return chain >= 0 && size_t(chain) < c->chains.size(); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+namespace mg {
+bool supported_n(int n) { return is_supported_n(n); }
+
+int yz_cluster_choices(int n, int precision, int* out, int max_out) {
+  std::vector<int> v;
+  if (precision == 32) {
+    if (n == 256) v = {2, 4};
+    else if (n == 192) v = {1, 2};
+    else if (n == 128) v = {1, 2};
+    else v = {1};
+  } else {
+    if (n == 256) v = {4};
+    else if (n == 192) v = {2};
+    else v = {1};
+  }
+  int k = 0;
+  for (int c : v)
+    if (k < max_out) out[k++] = c;
+  return k;
+}
+}  // namespace mg
+
+extern "C" {
+
+void mg_options_init(mg_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = 64;
+  o->n_chains = 1;
+  o->chain_id0 = 0;
+  o->tau_scale = 1.0;
+  o->P0 = nullptr;
+  o->record_every = 0;
+  o->fix_P = 0;
+  o->timeout_cycles = 0;
+  o->cuda_stream = nullptr;
+  o->yz_cluster = 0;
+}
+
+mg_status mg_init(mg_ctx** out, const mg_grid* grid, const double* N, const double* R, const double* d,
+                  const double* k_edges, int32_t n_bins, uint64_t seed, const mg_options* opt) {
+  const double* Np[1] = {N};
+  const double* Rp[1] = {R};
+  const double* dp[1] = {d};
+  const double* ep[1] = {k_edges};
+  return create(out, 1, grid, Np, Rp, dp, ep, &n_bins, &seed, opt);
+}
+
+mg_status mg_init_batch(mg_ctx** out, int32_t n_groups, const mg_grid* grids, const double* const* N,
+                        const double* const* R, const double* const* d, const double* const* k_edges,
+                        const int32_t* n_bins, const uint64_t* seeds, const mg_options* opt) {
+  return create(out, n_groups, grids, N, R, d, k_edges, n_bins, seeds, opt);
+}
+
+mg_status mg_sweep(mg_ctx* c, int64_t n) {
+  if (!c) return MG_EINVAL;
+  if (c->sticky != MG_OK) return c->sticky;
+  if (n < 0) return fail(c, MG_EINVAL, "n_sweeps must be >= 0");
+  for (int64_t i = 0; i < n; ++i) {
+    mg_status s = MG_OK;
+    if (!c->graph && !c->graph_failed) {
+      cudaGraph_t g;
+      if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        s = enqueue_sweep(c);
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (s == MG_OK && e == cudaSuccess) {
+          if (cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) {
+            c->graph = nullptr;
+            c->graph_failed = true;
+          }
+          cudaGraphDestroy(g);
+        } else {
+          c->graph_failed = true;
+          (void)cudaGetLastError();
+          if (s != MG_OK) return s;
+        }
+      } else {
+        c->graph_failed = true;
+        (void)cudaGetLastError();
+      }
+    }
+    if (c->graph) {
+      MG_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
+    } else {
+      s = enqueue_sweep(c);
+      if (s != MG_OK) return s;
+    }
+    ++c->sweeps;
+    if (c->record_every > 0 && c->sweeps % c->record_every == 0) {
+      s = c->precision == 32 ? record_stats<float>(c) : record_stats<double>(c);
+      if (s != MG_OK) return s;
+    }
+  }
+  return MG_OK;
+}
+
+mg_status mg_sweep_timed(mg_ctx* c, int64_t n, double* ms_out) {
+  if (!c || !ms_out) return MG_EINVAL;
+  if (c->sticky != MG_OK) return c->sticky;
+  if (n < 0) return fail(c, MG_EINVAL, "n_sweeps must be >= 0");
+  cudaEvent_t ev[4];
+  for (auto& e : ev) MG_CUDA(c, cudaEventCreate(&e));
+  for (int64_t i = 0; i < n; ++i) {
+    MG_CUDA(c, cudaEventRecord(ev[0], c->stream));
+    mg_status s = c->precision == 32 ? enqueue_passes<float>(c, 1) : enqueue_passes<double>(c, 1);
+    if (s != MG_OK) return s;
+    MG_CUDA(c, cudaEventRecord(ev[1], c->stream));
+    s = c->precision == 32 ? enqueue_passes<float>(c, 2) : enqueue_passes<double>(c, 2);
+    if (s != MG_OK) return s;
+    MG_CUDA(c, cudaEventRecord(ev[2], c->stream));
+    s = c->precision == 32 ? enqueue_passes<float>(c, 4) : enqueue_passes<double>(c, 4);
+    if (s != MG_OK) return s;
+    MG_CUDA(c, cudaEventRecord(ev[3], c->stream));
+    MG_CUDA(c, cudaEventSynchronize(ev[3]));
+    for (int k = 0; k < 3; ++k) {
+      float ms = 0.f;
+      MG_CUDA(c, cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+      ms_out[k] += double(ms);
+    }
+    ++c->sweeps;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return check_status(c);
+}
+
+mg_status mg_read_s(mg_ctx* c, int32_t chain, void* out, int32_t out_is_device) {
+  if (!c || !out) return MG_EINVAL;
+  if (c->sticky != MG_OK) return c->sticky;
+  if (!valid_chain(c, chain)) return fail(c, MG_EINVAL, "chain index out of range");
+  const Group& g = c->groups[c->chains[chain].group];
+  const size_t es = c->precision == 32 ? 4 : 8;
+  void* dst = out;
+  std::shared_ptr<DevBuf> tmp;
+  if (!out_is_device) {
+    cudaError_t e;
+    tmp = dalloc(g.M * es, &e);
+    MG_CUDA(c, e);
+    dst = tmp->p;
+  }
+  const mg_status s = c->precision == 32 ? materialize<float>(c, chain, static_cast<float*>(dst))
+                                         : materialize<double>(c, chain, static_cast<double*>(dst));
+  if (s != MG_OK) return s;
+  if (!out_is_device) {
+    MG_CUDA(c, cudaMemcpyAsync(out, dst, g.M * es, cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return check_status(c);
+}
+
+mg_status mg_read_pk(mg_ctx* c, int32_t chain, double* out) {
+  if (!c || !out) return MG_EINVAL;
+  if (!valid_chain(c, chain)) return fail(c, MG_EINVAL, "chain index out of range");
+  const Group& g = c->groups[c->chains[chain].group];
+  MG_CUDA(c, cudaMemcpyAsync(out, c->chains[chain].P->p, size_t(g.B + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
+mg_status mg_read_stats(mg_ctx* c, int32_t chain, mg_stats* out) {
+  if (!c || !out) return MG_EINVAL;
+  if (!valid_chain(c, chain)) return fail(c, MG_EINVAL, "chain index out of range");
+  const Chain& ch = c->chains[chain];
+  const Group& g = c->groups[ch.group];
+  out->sweeps = c->sweeps;
+  out->records = c->records;
+  out->tau = g.tau;
+  out->n_bins = g.B;
+  if (out->n_b) std::memcpy(out->n_b, g.n_b.data(), g.n_b.size() * sizeof(long long));
+  const size_t nb = size_t(g.B + 1) * sizeof(double);
+  if (out->sigma_b) MG_CUDA(c, cudaMemcpyAsync(out->sigma_b, ch.sig->p, nb, cudaMemcpyDeviceToHost, c->stream));
+  if (out->chi_b) MG_CUDA(c, cudaMemcpyAsync(out->chi_b, ch.chi->p, nb, cudaMemcpyDeviceToHost, c->stream));
+  if (out->mean || out->var) {
+    if (c->record_every <= 0) return fail(c, MG_ESTATE, "mean/var need record_every > 0");
+    if (out->mean)
+      MG_CUDA(c, cudaMemcpyAsync(out->mean, ch.mean->p, g.M * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (out->var) {
+      MG_CUDA(c, cudaMemcpyAsync(out->var, ch.m2->p, g.M * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (out->var) {
+    const double inv = c->records > 1 ? 1.0 / double(c->records - 1) : 0.0;
+    for (size_t i = 0; i < g.M; ++i) out->var[i] *= inv;
+  }
+  return check_status(c);
+}
+
+mg_status mg_set_s(mg_ctx* c, int32_t chain, const void* s_in, int32_t s_is_device) {
+  if (!c || !s_in) return MG_EINVAL;
+  if (c->sticky != MG_OK) return c->sticky;
+  if (!valid_chain(c, chain)) return fail(c, MG_EINVAL, "chain index out of range");
+  const Group& g = c->groups[c->chains[chain].group];
+  const size_t es = c->precision == 32 ? 4 : 8;
+  const void* src = s_in;
+  std::shared_ptr<DevBuf> tmp;
+  if (!s_is_device) {
+    cudaError_t e;
+    tmp = dalloc(g.M * es, &e);
+    MG_CUDA(c, e);
+    MG_CUDA(c, cudaMemcpyAsync(tmp->p, s_in, g.M * es, cudaMemcpyHostToDevice, c->stream));
+    src = tmp->p;
+  }
+  const mg_status s = c->precision == 32 ? load_s<float>(c, chain, static_cast<const float*>(src))
+                                         : load_s<double>(c, chain, static_cast<const double*>(src));
+  if (s != MG_OK) return s;
+  return check_status(c);
+}
+
+mg_status mg_set_pk(mg_ctx* c, int32_t chain, const double* P) {
+  if (!c || !P) return MG_EINVAL;
+  if (c->sticky != MG_OK) return c->sticky;
+  if (!valid_chain(c, chain)) return fail(c, MG_EINVAL, "chain index out of range");
+  const Group& g = c->groups[c->chains[chain].group];
+  for (int b = 0; b <= g.B; ++b)
+    if (!(P[b] > 0.0) || !std::isfinite(P[b])) return fail(c, MG_EINVAL, "P must be positive and finite");
+  MG_CUDA(c, cudaMemcpyAsync(c->chains[chain].P->p, P, size_t(g.B + 1) * sizeof(double), cudaMemcpyHostToDevice,
+                             c->stream));
+  const mg_status s = c->precision == 32 ? launch_shell_draw<float>(c, 0, false) : launch_shell_draw<double>(c, 0, false);
+  if (s != MG_OK) return s;
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
+mg_status mg_get_sweep_count(mg_ctx* c, int64_t* out) {
+  if (!c || !out) return MG_EINVAL;
+  uint32_t v = 0;
+  MG_CUDA(c, cudaMemcpyAsync(&v, c->d_sweep->p, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  *out = int64_t(v);
+  return MG_OK;
+}
+
+mg_status mg_set_sweep_count(mg_ctx* c, int64_t sweeps) {
+  if (!c) return MG_EINVAL;
+  if (sweeps < 0 || sweeps > 0xffffffffll) return fail(c, MG_EINVAL, "sweep count out of range");
+  const uint32_t v = uint32_t(sweeps);
+  MG_CUDA(c, cudaMemcpyAsync(c->d_sweep->p, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->sweeps = sweeps;
+  return MG_OK;
+}
+
+mg_status mg_chain_info(mg_ctx* c, int32_t chain, int32_t* n, int32_t* n_bins, int32_t* n_chains) {
+  if (!c) return MG_EINVAL;
+  if (n_chains) *n_chains = int32_t(c->chains.size());
+  if (n || n_bins) {
+    if (!valid_chain(c, chain)) return fail(c, MG_EINVAL, "chain index out of range");
+    const Group& g = c->groups[c->chains[chain].group];
+    if (n) *n = g.n;
+    if (n_bins) *n_bins = g.B;
+  }
+  return MG_OK;
+}
+
+mg_status mg_sync(mg_ctx* c) {
+  if (!c) return MG_EINVAL;
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
+const char* mg_last_error(const mg_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+void mg_destroy(mg_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->classes.clear();
+  c->chains.clear();
+  c->groups.clear();
+  c->d_draw.reset();
+  c->d_sweep.reset();
+  c->d_status.reset();
+  c->d_scratch_s.reset();
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+mg_status mg_philox(uint64_t seed, uint32_t ctr0, uint32_t ctr1, uint32_t ctr2, uint32_t ctr3, int64_t n_calls,
+                    uint32_t* out_device, void* stream) {
+  if (n_calls < 0 || (n_calls > 0 && !out_device)) return MG_EINVAL;
+  if (n_calls == 0) return MG_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int blocks = int(std::min<int64_t>((n_calls + 255) / 256, 4096));
+  philox_fill_kernel<<<blocks, 256, 0, st>>>(uint32_t(seed & 0xffffffffu), uint32_t(seed >> 32), ctr0, ctr1, ctr2,
+                                              ctr3, (long long)n_calls, reinterpret_cast<uint4*>(out_device));
+  if (cudaGetLastError() != cudaSuccess) return MG_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MG_ECUDA;
+  return MG_OK;
+}
+
+}  // extern "C"

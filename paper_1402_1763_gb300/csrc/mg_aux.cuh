@@ -1,0 +1,170 @@
+// Small kernels around the two sweep passes: set-up of the messenger
+// constants (Sec. 2 and the t-conditional of Sec. 3.1), the per-shell
+// inverse-gamma draw (Sec. 3.2, Alg. 2 on shells), chain statistics and the
+// raw Philox fill used to check the generator bit for bit.
+#pragma once
+#include "mg_device.cuh"
+
+namespace mg {
+
+// tau bound: min over observed voxels of N_i / R_i^2 (Sec. 2, diagonal R).
+// Positive doubles order like their bit patterns, so the minimum is an
+// integer atomicMin and independent of the order of the updates.  Also flags
+// invalid inputs (R < 0, N <= 0 where R > 0, non-finite) and counts observed
+// voxels.
+__global__ void tau_bound_kernel(const double* __restrict__ N, const double* __restrict__ R,
+                                 const double* __restrict__ d, size_t M, unsigned long long* min_bits,
+                                 unsigned long long* n_obs, int* status) {
+  unsigned long long local_min = 0x7FF0000000000000ull;  // +inf
+  unsigned long long local_obs = 0;
+  int bad = 0;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < M; i += size_t(gridDim.x) * blockDim.x) {
+    const double r = R[i], n = N[i], dd = d[i];
+    if (!(r >= 0.0) || !isfinite(r)) bad = 1;
+    if (r > 0.0) {
+      if (!(n > 0.0) || !isfinite(n) || !isfinite(dd)) bad = 1;
+      const double q = __ddiv_rn(n, __dmul_rn(r, r));
+      if (q > 0.0 && isfinite(q)) {
+        const unsigned long long b = __double_as_longlong(q);
+        local_min = b < local_min ? b : local_min;
+      } else {
+        bad = 1;
+      }
+      ++local_obs;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_down_sync(0xffffffffu, local_min, off);
+    local_min = o < local_min ? o : local_min;
+    local_obs += __shfl_down_sync(0xffffffffu, local_obs, off);
+    bad |= __shfl_down_sync(0xffffffffu, bad, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(min_bits, local_min);
+    atomicAdd(n_obs, local_obs);
+    if (bad) atomicOr(status, kStBadInput);
+  }
+}
+
+// Per-voxel constants of the messenger draw t = c + b s + sqrt(tau b) g:
+//   observed:   N~ = max(N - R tau R, 0), b = N~ / (tau R^2 + N~),
+//               c = tau / (tau R^2 + N~) * R * d
+//   unobserved: b = 1, c = 0   (mu = s, sigma^2 = T).
+// Products and sums are rounded one by one (no FMA contraction).
+template <typename T>
+__global__ void messenger_constants_kernel(const double* __restrict__ N, const double* __restrict__ R,
+                                           const double* __restrict__ d, size_t M, double tau,
+                                           typename VT<T>::c2* __restrict__ bc) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < M; i += size_t(gridDim.x) * blockDim.x) {
+    const double r = R[i];
+    double b = 1.0, c = 0.0;
+    if (__dmul_rn(r, r) > 0.0) {
+      double nt = __dsub_rn(N[i], __dmul_rn(__dmul_rn(r, tau), r));
+      nt = nt > 0.0 ? nt : 0.0;
+      const double den = __dadd_rn(__dmul_rn(tau, __dmul_rn(r, r)), nt);
+      b = __ddiv_rn(nt, den);
+      c = __dmul_rn(__dmul_rn(__ddiv_rn(tau, den), r), d[i]);
+    }
+    typename VT<T>::c2 v;
+    v.x = T(b);
+    v.y = T(c);
+    bc[i] = v;
+  }
+}
+
+// Shell draw and the next sweep's per-shell coefficients.  One CTA per
+// (chain, shell): sum the per-tile partials in a fixed order (deterministic),
+// then S_b = sigma_b / X_b with X_b ~ chi^2_{n_b}, i.e. S_b | s ~
+// InvGamma(n_b/2, sigma_b/2) from Jeffreys' prior (Sec. 3.2); P_b = (V/M) S_b.
+// Empty shells, and shells whose sums are not positive and finite (flagged),
+// keep their P.  Then a_b = S/(S + tau), sd_b = sqrt(S tau / (S + tau))
+// (Sec. 3.1), stored as (a_b / sqrt(M), sd_b) for pass X; the DC entry is 0.
+// draw = 0: only recompute the coefficients from P (set-up, mg_set_pk).
+// fix_P != 0: sum the shells but keep P (the signal sampler alone).
+template <typename T>
+__global__ void shell_draw_kernel(const DrawDev* __restrict__ chains, int draw, int fix_P, int* status,
+                                  uint32_t* sweep_ctr) {
+  const DrawDev cd = chains[blockIdx.x];
+  const int b = blockIdx.y;
+  if (b > cd.B) return;
+  const int B1 = cd.B + 1;
+  __shared__ double r1[256], r2[256];
+  double s1 = 0.0, s2 = 0.0;
+  if (draw) {
+    for (int t = threadIdx.x; t < cd.n_tiles; t += blockDim.x) {
+      s1 += cd.partial[(size_t(t) * B1 + b) * 2 + 0];
+      s2 += cd.partial[(size_t(t) * B1 + b) * 2 + 1];
+    }
+  }
+  r1[threadIdx.x] = s1;
+  r2[threadIdx.x] = s2;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      r1[threadIdx.x] += r1[threadIdx.x + w];
+      r2[threadIdx.x] += r2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  double P = cd.P[b];
+  if (draw) {
+    const double sig = r1[0], chi = r2[0];
+    cd.sig_last[b] = sig;
+    cd.chi_last[b] = chi;
+    if (!fix_P && cd.n_b[b] > 0) {
+      if (sig > 0.0 && chi > 0.0 && isfinite(sig) && isfinite(chi)) {
+        P = (cd.V / cd.M) * sig / chi;
+      } else {
+        atomicOr(status, kStNumeric);
+      }
+    }
+    cd.P[b] = P;
+  }
+  const double Sh = (cd.M / cd.V) * P;
+  const double a = Sh / (Sh + cd.tau);
+  const double sd = sqrt(Sh * cd.tau / (Sh + cd.tau));
+  typename VT<T>::c2* coef = static_cast<typename VT<T>::c2*>(cd.coef);
+  typename VT<T>::c2 v;
+  v.x = T(a / sqrt(cd.M));
+  v.y = T(sd);
+  coef[b] = v;
+  if (b == 0) {
+    v.x = T(0);
+    v.y = T(0);
+    coef[cd.B + 1] = v;
+  }
+  if (sweep_ctr && blockIdx.x == 0 && b == 0) atomicAdd(sweep_ctr, 1u);
+}
+
+// Welford update of the per-voxel mean and sum of squared deviations of s.
+template <typename T>
+__global__ void welford_kernel(const T* __restrict__ s, double* __restrict__ mean, double* __restrict__ m2,
+                               size_t M, double inv_count) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < M; i += size_t(gridDim.x) * blockDim.x) {
+    const double x = double(s[i]);
+    const double mu = mean[i];
+    const double dlt = x - mu;
+    const double mu2 = mu + dlt * inv_count;
+    mean[i] = mu2;
+    m2[i] += dlt * (x - mu2);
+  }
+}
+
+// Append each chain's P to its trace: trace[chain][slot][b].
+__global__ void trace_kernel(const DrawDev* __restrict__ chains, double* const* traces, int slot) {
+  const DrawDev cd = chains[blockIdx.x];
+  double* tr = traces[blockIdx.x];
+  for (int b = threadIdx.x; b <= cd.B; b += blockDim.x) tr[size_t(slot) * (cd.B + 1) + b] = cd.P[b];
+}
+
+__global__ void philox_fill_kernel(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                   long long n, uint4* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const u32x4 w = philox4x32_10(c0 + uint32_t(i), c1, c2, c3, k0, k1);
+    out[i] = make_uint4(w.x, w.y, w.z, w.w);
+  }
+}
+
+}  // namespace mg

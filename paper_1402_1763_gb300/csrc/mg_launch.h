@@ -1,0 +1,29 @@
+// Host-side launchers of the sweep kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mg_device.cuh"
+
+namespace mg {
+
+// Grid sizes the kernels are compiled for: n = 2^a 3^b, 8 <= n <= 256, n % 4 == 0.
+bool supported_n(int n);
+
+// Pass YZ cluster sizes compiled for (n, precision); the first is the default.
+int yz_cluster_choices(int n, int precision, int* out, int max_out);
+size_t yz_smem_bytes(int n, int C, int precision);
+
+// n_chains == 0 only sets the kernels' attributes (done once, outside any
+// stream capture).
+template <typename T>
+cudaError_t launch_pass_yz(int n, int C, int mode, const ChainDev<T>* d_chains, int n_chains,
+                           const uint32_t* d_sweep, const void* tw, cudaStream_t st);
+
+int pass_x_tiles(int n);
+template <typename T>
+cudaError_t launch_pass_x(int n, const ChainDev<T>* d_chains, int n_chains, const uint32_t* d_sweep,
+                          const void* tw, int B_max, cudaStream_t st);
+
+}  // namespace mg

@@ -1,0 +1,63 @@
+// Instantiations and launcher of pass X (see mg_pass_x.cuh).
+#include "mg_launch.h"
+#include "mg_pass_x.cuh"
+
+namespace mg {
+
+namespace {
+template <int N>
+constexpr int pass_x_threads() {
+  // threads per CTA: 32 pencils x (threads per pencil)
+  return N >= 128 ? 256 : (N >= 32 ? 128 : 64);
+}
+
+template <typename T, int N>
+cudaError_t run_x(const ChainDev<T>* d_chains, int n_chains, const uint32_t* d_sweep, const void* tw,
+                  int B_max, cudaStream_t st) {
+  constexpr int NT = pass_x_threads<N>();
+  using S = PassXShape<T, N>;
+  const size_t smem = S::smem_bytes(NT / 32, B_max);
+  auto kern = pass_x_kernel<T, N, NT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess || n_chains == 0) return e;  // n_chains == 0: set attributes only
+  const unsigned grid = unsigned(S::kTiles) * unsigned(n_chains);
+  kern<<<grid, NT, smem, st>>>(d_chains, d_sweep, static_cast<const typename VT<T>::c2*>(tw));
+  return cudaGetLastError();
+}
+}  // namespace
+
+int pass_x_tiles(int n) {
+  const int lw = 32;
+  return (n * (n / 2) + lw - 1) / lw + (n + lw - 1) / lw;
+}
+
+template <typename T>
+cudaError_t launch_pass_x(int n, const ChainDev<T>* d_chains, int n_chains, const uint32_t* d_sweep,
+                          const void* tw, int B_max, cudaStream_t st) {
+  switch (n) {
+#define MG_CASE(N_) \
+  case N_:          \
+    return run_x<T, N_>(d_chains, n_chains, d_sweep, tw, B_max, st);
+    MG_CASE(8)
+    MG_CASE(12)
+    MG_CASE(16)
+    MG_CASE(24)
+    MG_CASE(32)
+    MG_CASE(48)
+    MG_CASE(64)
+    MG_CASE(96)
+    MG_CASE(128)
+    MG_CASE(192)
+    MG_CASE(256)
+#undef MG_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_pass_x<float>(int, const ChainDev<float>*, int, const uint32_t*, const void*, int,
+                                          cudaStream_t);
+template cudaError_t launch_pass_x<double>(int, const ChainDev<double>*, int, const uint32_t*, const void*, int,
+                                           cudaStream_t);
+
+}  // namespace mg

@@ -1,0 +1,281 @@
+// Pass X of the two-pass sweep: forward x-FFT, the signal draw per mode,
+// the k-shell sums, and the inverse x-FFT, on tiles of 32 x-pencils.
+//
+//   * signal draw (Sec. 3.1, Alg. 1 second loop): s_hat = mu + sigma xi with
+//     mu = S/(S + T) t_hat and sigma^2 = S T/(S + T), T = tau for the unitary
+//     transform; S_hat = (M/V) P(shell) and 0 at k = 0.
+//   * shell sums for the covariance draw (Sec. 3.2, Alg. 2 on shells):
+//     sigma_b = sum w |s_hat|^2 and X_b = sum of w squared unit normals.
+//
+// A CTA owns 32 consecutive pencils (lanes) and all n values of x.  The FFT of
+// length n = P*Q runs as: stage F1 (DFT_Q per p, from global), exchange through
+// shared memory, stage F2 (DFT_P per v) -> modes kx = Q u + v in registers ->
+// draw -> inverse stage I1 (IDFT_P) back into the same shared slots -> stage
+// I2 (IDFT_Q per p) -> global.  Warp lanes are pencils at the same kx, so the
+// shell ids along a warp come in runs, reduced with a segmented warp scan.
+#pragma once
+#include "mg_device.cuh"
+
+namespace mg {
+
+// Shell accumulators per warp: FP32 keeps an error-free (hi, lo) FP32 pair per
+// value (TwoSum), FP64 a plain double; both are combined in FP64 per tile.
+template <typename T>
+struct Acc;
+template <>
+struct Acc<float> {
+  static constexpr int kWords = 4;  // hi1, lo1, hi2, lo2
+  static __device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += e;
+  }
+  static __device__ __forceinline__ void add(float* a, float x1, float x2) {
+    float h1 = a[0], l1 = a[1], h2 = a[2], l2 = a[3];
+    two_sum(h1, l1, x1);
+    two_sum(h2, l2, x2);
+    a[0] = h1;
+    a[1] = l1;
+    a[2] = h2;
+    a[3] = l2;
+  }
+};
+template <>
+struct Acc<double> {
+  static constexpr int kWords = 2;
+  static __device__ __forceinline__ void add(double* a, double x1, double x2) {
+    a[0] += x1;
+    a[1] += x2;
+  }
+};
+
+// Segmented warp reduction of (v1, v2) over runs of equal shell id, then the
+// head of each run adds the run's sums to this warp's accumulators.  bin < 0
+// marks lanes that contribute nothing.
+template <typename T>
+__device__ __forceinline__ void shell_accumulate(T v1, T v2, int bin, T* accw, int lane) {
+  const unsigned full = 0xffffffffu;
+  const int prevb = __shfl_up_sync(full, bin, 1);
+  const bool head = (lane == 0) || (prevb != bin);
+  const unsigned heads = __ballot_sync(full, head);
+  const unsigned later = (lane == 31) ? 0u : (heads & (full << (lane + 1)));
+  const int run_end = later ? (__ffs(later) - 2) : 31;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const T o1 = __shfl_down_sync(full, v1, off);
+    const T o2 = __shfl_down_sync(full, v2, off);
+    if (lane + off <= run_end) {
+      v1 += o1;
+      v2 += o2;
+    }
+  }
+  const bool writer = head && bin >= 0;
+  const int key = writer ? bin : (-1000 - lane);
+  const unsigned same = __match_any_sync(full, key);
+  const bool dup = writer && (__popc(same) > 1);
+  if (!__any_sync(full, dup)) {
+    if (writer) Acc<T>::add(accw + bin * Acc<T>::kWords, v1, v2);
+  } else {
+    unsigned hm = __ballot_sync(full, writer);
+    while (hm) {
+      const int src = __ffs(hm) - 1;
+      if (lane == src) Acc<T>::add(accw + bin * Acc<T>::kWords, v1, v2);
+      __syncwarp();
+      hm &= hm - 1;
+    }
+  }
+}
+
+// The signal draw of one stored mode (kx, ky, kz).  F is the unnormalised
+// forward DFT of t, i.e. sqrt(M) t_hat.  Returns s_hat / sqrt(M), the value the
+// unnormalised inverse transforms turn into s; reports the shell id (or -1) and
+// the mode's contributions w |s_hat|^2 and its w squared normals.
+template <typename T, int N>
+__device__ __forceinline__ cx<T> draw_mode(cx<T> F, int kx, int ky, int kz, bool valid,
+                                           const ChainDev<T>& cd, uint32_t sweep, T inv_sqrtM,
+                                           int& bin, T& sig, T& chi) {
+  constexpr int H = N / 2;
+  const int mx = kx <= H ? kx : kx - N;
+  const int my = ky <= H ? ky : ky - N;
+  const int m2 = mx * mx + my * my + kz * kz;
+  const uint32_t j = uint32_t((kx * N + ky) * (H + 1) + kz);
+  const bool edge = (kz == 0) || (kz == H);
+  const u32x4 w = philox4x32_10(j, sweep, cd.chain_id, kStreamModes, cd.k0, cd.k1);
+  T z0, z1, z2, z3;
+  box_muller(w.x, w.y, z0, z1);
+  box_muller(w.z, w.w, z2, z3);
+  const T rs2 = T(0.70710678118654752440);
+  cx<T> xi;
+  T wgt;
+  if (!edge) {
+    xi = {z0 * rs2, z1 * rs2};
+    chi = z2 * z2 + z3 * z3;
+    wgt = T(2);
+  } else {
+    chi = z2 * z2;
+    wgt = T(1);
+    const uint32_t jp = uint32_t(((((N - kx) % N) * N) + ((N - ky) % N)) * (H + 1) + kz);
+    if (jp == j) {
+      xi = {z0, T(0)};
+    } else if (j < jp) {
+      xi = {z0 * rs2, z1 * rs2};
+    } else {
+      const u32x4 wp = philox4x32_10(jp, sweep, cd.chain_id, kStreamModes, cd.k0, cd.k1);
+      T p0, p1;
+      box_muller(wp.x, wp.y, p0, p1);
+      xi = {p0 * rs2, -(p1 * rs2)};
+    }
+  }
+  const bool dc = (m2 == 0);
+  bin = dc ? -1 : int(__ldg(cd.bin_of_m2 + m2));
+  const cx<T> cf = ldc<T>(cd.coef + (dc ? cd.B + 1 : bin));
+  const cx<T> s = {cf.re * F.re + cf.im * xi.re, cf.re * F.im + cf.im * xi.im};
+  sig = wgt * (s.re * s.re + s.im * s.im);
+  if (!valid || dc) {
+    bin = -1;
+    sig = T(0);
+    chi = T(0);
+  }
+  return {s.re * inv_sqrtM, s.im * inv_sqrtM};
+}
+
+template <typename T, int N>
+struct PassXShape {
+  static constexpr int H = N / 2;
+  static constexpr int P = Split<N>::P, Q = Split<N>::Q;
+  static constexpr int LW = 32;
+  static constexpr int kMainTiles = (N * H + LW - 1) / LW;
+  static constexpr int kNyqTiles = (N + LW - 1) / LW;
+  static constexpr int kTiles = kMainTiles + kNyqTiles;
+  static constexpr size_t kXchgBytes = size_t(N) * LW * sizeof(typename VT<T>::c2);
+  static size_t smem_bytes(int nwarps, int B) {
+    return kXchgBytes + size_t(nwarps) * (B + 1) * Acc<T>::kWords * sizeof(T);
+  }
+};
+
+template <typename T, int N, int NT>
+__global__ void __launch_bounds__(NT) pass_x_kernel(const ChainDev<T>* __restrict__ chains,
+                                                    const uint32_t* __restrict__ sweep_ctr,
+                                                    const typename VT<T>::c2* __restrict__ tw) {
+  using S = PassXShape<T, N>;
+  using V2 = typename VT<T>::c2;
+  constexpr int H = S::H, P = S::P, Q = S::Q, LW = S::LW;
+  constexpr int NW = NT / 32;
+  static_assert(NT % 32 == 0, "whole warps");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V2* xs = reinterpret_cast<V2*>(smem_raw);  // [N][LW], slot p*Q + v
+  T* acc = reinterpret_cast<T*>(smem_raw + S::kXchgBytes);
+
+  const int tile = blockIdx.x % S::kTiles;
+  const int chain = blockIdx.x / S::kTiles;
+  const ChainDev<T> cd = chains[chain];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int B1 = cd.B + 1;
+  const uint32_t sweep = *sweep_ctr;
+  const T inv_sqrtM = T(1.0 / sqrt(double(N) * double(N) * double(N)));
+
+  for (int i = threadIdx.x; i < NW * B1 * Acc<T>::kWords; i += NT) acc[i] = T(0);
+
+  const bool nyq_tile = tile >= S::kMainTiles;
+  int ky, kz;
+  bool valid;
+  V2* base;
+  size_t stride;
+  if (!nyq_tile) {
+    const int f = tile * LW + lane;
+    valid = f < N * H;
+    ky = valid ? f / H : 0;
+    kz = valid ? f % H : 0;
+    base = cd.main + (valid ? f : 0);
+    stride = size_t(N) * H;
+  } else {
+    ky = (tile - S::kMainTiles) * LW + lane;
+    valid = ky < N;
+    if (!valid) ky = 0;
+    kz = H;
+    base = cd.nyq + ky;
+    stride = N;
+  }
+
+  // Stage F1: DFT_Q over q of x[p + P q], twiddle W_N^{p v}, to slot p*Q + v.
+  for (int it = threadIdx.x; it < LW * P; it += NT) {
+    const int p = it / LW;
+    cx<T> v[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) v[q] = valid ? ldc<T>(base + size_t(p + P * q) * stride) : cx<T>{T(0), T(0)};
+    Dft<Q, -1, T>::run(v);
+#pragma unroll
+    for (int vq = 0; vq < Q; ++vq) {
+      const cx<T> y = vq == 0 ? v[vq] : cmul(v[vq], ldc<T>(tw + p * vq));
+      stc<T>(xs + (p * Q + vq) * LW + lane, y);
+    }
+  }
+  __syncthreads();
+
+  // Stage F2 + draw + inverse stage I1, in place in the slots of column v.
+  T* accw = acc + warp * B1 * Acc<T>::kWords;
+  for (int it = threadIdx.x; it < LW * Q; it += NT) {
+    const int vq = it / LW;
+    cx<T> X[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs + (p * Q + vq) * LW + lane);
+    Dft<P, -1, T>::run(X);
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      int bin;
+      T sg, ch;
+      X[u] = draw_mode<T, N>(X[u], Q * u + vq, ky, kz, valid, cd, sweep, inv_sqrtM, bin, sg, ch);
+      shell_accumulate<T>(sg, ch, bin, accw, lane);
+    }
+    Dft<P, +1, T>::run(X);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const cx<T> y = (p * vq == 0) ? X[p] : cmulc(X[p], ldc<T>(tw + p * vq));
+      stc<T>(xs + (p * Q + vq) * LW + lane, y);
+    }
+  }
+  __syncthreads();
+
+  // Stage I2: IDFT_Q over v of slot p*Q + v, out to x = p + P q.
+  for (int it = threadIdx.x; it < LW * P; it += NT) {
+    const int p = it / LW;
+    cx<T> v[Q];
+#pragma unroll
+    for (int vq = 0; vq < Q; ++vq) v[vq] = ldc<T>(xs + (p * Q + vq) * LW + lane);
+    Dft<Q, +1, T>::run(v);
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) stc<T>(base + size_t(p + P * q) * stride, v[q]);
+    }
+  }
+
+  // Per-tile shell sums: combine the warps in a fixed order, then FP64.
+  double* part = cd.partial + size_t(tile) * B1 * 2;
+  for (int b = threadIdx.x; b < B1; b += NT) {
+    if constexpr (sizeof(T) == 4) {
+      float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+      for (int w2 = 0; w2 < NW; ++w2) {
+        const float* a = acc + (w2 * B1 + b) * 4;
+        Acc<float>::two_sum(h1, l1, a[0]);
+        l1 += a[1];
+        Acc<float>::two_sum(h2, l2, a[2]);
+        l2 += a[3];
+      }
+      part[2 * b + 0] = double(h1) + double(l1);
+      part[2 * b + 1] = double(h2) + double(l2);
+    } else {
+      double s1 = 0.0, s2 = 0.0;
+      for (int w2 = 0; w2 < NW; ++w2) {
+        const double* a = acc + (w2 * B1 + b) * 2;
+        s1 += a[0];
+        s2 += a[1];
+      }
+      part[2 * b + 0] = s1;
+      part[2 * b + 1] = s2;
+    }
+  }
+}
+
+}  // namespace mg

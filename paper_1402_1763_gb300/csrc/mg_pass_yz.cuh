@@ -1,0 +1,324 @@
+// Pass YZ of the two-pass sweep, one x-plane per CTA cluster:
+//   inverse y-FFT and C2R z-FFT of the previous signal s_hat -> s (real plane)
+//   -> messenger draw t | s, d per voxel (Sec. 3.1, Alg. 1 first loop)
+//   -> R2C z-FFT and forward y-FFT of t.
+//
+// The plane (n rows of n/2 packed complex values: column 0 carries the kz = 0
+// and kz = n/2 planes as its real and imaginary parts) lives in shared memory,
+// split by rows over the C CTAs of a thread-block cluster when it does not fit
+// one CTA; column stages reach the other CTAs' rows through distributed shared
+// memory.  Every stage reads a set of slots into registers, transforms them and
+// writes the results back into the same set of slots, so stages need a barrier
+// between them but no second buffer.
+//
+// Layouts (n = P Q along y, n/2 = P2 Q2 along z):
+//   row slot s = p*Q + q holds y = p + P q (the order the y-stages produce);
+//   within a row, column l is kz (packed at l = 0).
+#pragma once
+#include <cooperative_groups.h>
+
+#include "mg_device.cuh"
+
+namespace mg {
+
+namespace cg = cooperative_groups;
+
+enum PassYZMode : int {
+  kModeSweep = 0,        // inverse -> messenger draw -> forward (the hot path)
+  kModeMaterialize = 1,  // inverse only, write s to ChainDev::s_out
+  kModeLoad = 2,         // read s from ChainDev::s_in, forward only
+};
+
+template <typename T, int N, int C>
+struct PassYZShape {
+  static constexpr int H = N / 2;
+  static constexpr int P = Split<N>::P, Q = Split<N>::Q;
+  static constexpr int P2 = Split<H>::P, Q2 = Split<H>::Q;
+  static constexpr int ROWS = N / C;
+  static constexpr int RS = H + 1;  // padded row stride (complex elements)
+  static constexpr int PC = P / C, QC = Q / C;
+  static_assert(P % C == 0 && Q % C == 0, "cluster size must divide both y factors");
+  static_assert(P2 % 2 == 0, "row stage pairs adjacent p");
+  static constexpr size_t kSmemBytes = (size_t(ROWS) * RS + N) * sizeof(typename VT<T>::c2);
+};
+
+template <int C>
+__device__ __forceinline__ void cluster_barrier() {
+  if constexpr (C == 1) {
+    __syncthreads();
+  } else {
+    cg::this_cluster().sync();
+  }
+}
+
+template <typename T, int N, int C, int MODE, int NT>
+__global__ void __launch_bounds__(NT) pass_yz_kernel(const ChainDev<T>* __restrict__ chains, int n_chains,
+                                                     const uint32_t* __restrict__ sweep_ctr,
+                                                     const typename VT<T>::c2* __restrict__ tw) {
+  using S = PassYZShape<T, N, C>;
+  using V2 = typename VT<T>::c2;
+  constexpr int H = S::H, P = S::P, Q = S::Q, P2 = S::P2, Q2 = S::Q2;
+  constexpr int ROWS = S::ROWS, RS = S::RS, PC = S::PC, QC = S::QC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V2* rows = reinterpret_cast<V2*>(smem_raw);
+  V2* col0 = rows + ROWS * RS;
+
+  unsigned rank = 0;
+  V2* rbase[C];
+  V2* col0_r0;
+  if constexpr (C == 1) {
+    rbase[0] = rows;
+    col0_r0 = col0;
+  } else {
+    cg::cluster_group cl = cg::this_cluster();
+    rank = cl.block_rank();
+#pragma unroll
+    for (int r = 0; r < C; ++r) rbase[r] = cl.map_shared_rank(rows, r);
+    col0_r0 = cl.map_shared_rank(col0, 0);
+  }
+  const int unit = blockIdx.x / C;
+  const int x = unit / n_chains;
+  const int chain = unit % n_chains;
+  const ChainDev<T> cd = chains[chain];
+  V2* mainp = cd.main + size_t(x) * N * H;
+  V2* nyqp = cd.nyq + size_t(x) * N;
+  const uint32_t sweep = *sweep_ctr;
+  const T tau = cd.tau;
+
+  if constexpr (C > 1) cluster_barrier<C>();  // every CTA of the cluster is running
+
+  if constexpr (MODE != kModeLoad) {
+    // Column stage I1 (per v of this CTA): IDFT_P over u of X[Q u + v] from
+    // global, twiddle W_N^{-p v}, to slot p*Q + v (whichever CTA owns it).
+    for (int it = threadIdx.x; it < H * QC; it += NT) {
+      const int l = it % H;
+      const int v = int(rank) * QC + it / H;
+      cx<T> X[P];
+#pragma unroll
+      for (int u = 0; u < P; ++u) X[u] = ldc<T>(mainp + size_t(Q * u + v) * H + l);
+      if (l == 0) {
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+          const cx<T> b = ldc<T>(nyqp + Q * u + v);
+          X[u] = {X[u].re - b.im, X[u].im + b.re};
+        }
+      }
+      Dft<P, +1, T>::run(X);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const cx<T> y = (p * v == 0) ? X[p] : cmulc(X[p], ldc<T>(tw + p * v));
+        // slot p*Q + v lives in CTA p / PC at local row (p % PC)*Q + v
+        stc<T>(rbase[p / PC] + ((p % PC) * Q + v) * RS + l, y);
+      }
+    }
+    cluster_barrier<C>();
+
+    // Column stage I2 (per p of this CTA, local): IDFT_Q over v; y = p + P q
+    // goes to slot p*Q + q.
+    for (int it = threadIdx.x; it < H * PC; it += NT) {
+      const int l = it % H;
+      const int pl = it / H;  // local p index; slots pl*Q + v are local rows
+      cx<T> Z[Q];
+#pragma unroll
+      for (int v = 0; v < Q; ++v) Z[v] = ldc<T>(rows + (pl * Q + v) * RS + l);
+      Dft<Q, +1, T>::run(Z);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) stc<T>(rows + (pl * Q + q) * RS + l, Z[q]);
+    }
+    __syncthreads();
+
+    // Row pre-processing for the C2R z-transform through a half-length
+    // complex IDFT: Z'[k] = (X[k] + conj X[H-k]) + i W_n^{-k} (X[k] - conj X[H-k]).
+    for (int it = threadIdx.x; it < ROWS * (H / 2 + 1); it += NT) {
+      const int r = it % ROWS;
+      const int k = it / ROWS;
+      V2* row = rows + r * RS;
+      if (k == 0) {
+        const cx<T> z = ldc<T>(row);
+        stc<T>(row, cx<T>{z.re + z.im, z.re - z.im});
+      } else {
+        const int kk = H - k;
+        const cx<T> a = ldc<T>(row + k), b = ldc<T>(row + kk);
+        {
+          const cx<T> e = cadd(a, cconj(b)), d = csub(a, cconj(b));
+          stc<T>(row + k, cadd(e, cmul_i<+1>(cmulc(d, ldc<T>(tw + k)))));
+        }
+        if (kk != k) {
+          const cx<T> e = cadd(b, cconj(a)), d = csub(b, cconj(a));
+          stc<T>(row + kk, cadd(e, cmul_i<+1>(cmulc(d, ldc<T>(tw + kk)))));
+        }
+      }
+    }
+    __syncthreads();
+
+    // Row stage I1 (per v2): IDFT_P2 over u of Z'[Q2 u + v2], twiddle
+    // W_{n/2}^{-p v2} = W_n^{-2 p v2}, back to column p*Q2 + v2.
+    for (int it = threadIdx.x; it < ROWS * Q2; it += NT) {
+      const int r = it % ROWS;
+      const int v = it / ROWS;
+      V2* row = rows + r * RS;
+      cx<T> X[P2];
+#pragma unroll
+      for (int u = 0; u < P2; ++u) X[u] = ldc<T>(row + Q2 * u + v);
+      Dft<P2, +1, T>::run(X);
+#pragma unroll
+      for (int p = 0; p < P2; ++p) {
+        const cx<T> y = (p * v == 0) ? X[p] : cmulc(X[p], ldc<T>(tw + 2 * p * v));
+        stc<T>(row + p * Q2 + v, y);
+      }
+    }
+    __syncthreads();
+  }
+
+  // Row stage I2 + messenger draw + forward stage F1, per pair (p, p+1):
+  // IDFT_Q2 gives z[m] = s[2m] + i s[2m+1] for m = p + P2 q, so a pair holds
+  // the four consecutive voxels 2m..2m+3 (m even) = one Philox call.
+  for (int it = threadIdx.x; it < ROWS * (P2 / 2); it += NT) {
+    const int r = it % ROWS;
+    const int pp = 2 * (it / ROWS);
+    V2* row = rows + r * RS;
+    const int sg = int(rank) * ROWS + r;
+    const int y = sg / Q + P * (sg % Q);
+    const size_t vox_row = (size_t(x) * N + y) * N;
+    cx<T> Z0[Q2], Z1[Q2];
+    if constexpr (MODE != kModeLoad) {
+#pragma unroll
+      for (int v = 0; v < Q2; ++v) {
+        Z0[v] = ldc<T>(row + pp * Q2 + v);
+        Z1[v] = ldc<T>(row + (pp + 1) * Q2 + v);
+      }
+      Dft<Q2, +1, T>::run(Z0);
+      Dft<Q2, +1, T>::run(Z1);
+    }
+#pragma unroll
+    for (int q = 0; q < Q2; ++q) {
+      const int z0 = 2 * (pp + P2 * q);  // voxels z0 .. z0+3
+      const size_t i0 = vox_row + z0;
+      if constexpr (MODE == kModeMaterialize) {
+        T* o = cd.s_out + i0;
+        o[0] = Z0[q].re;
+        o[1] = Z0[q].im;
+        o[2] = Z1[q].re;
+        o[3] = Z1[q].im;
+      } else if constexpr (MODE == kModeLoad) {
+        const T* si = cd.s_in + i0;
+        Z0[q] = {si[0], si[1]};
+        Z1[q] = {si[2], si[3]};
+      } else {
+        const u32x4 w = philox4x32_10(uint32_t(i0 >> 2), sweep, cd.chain_id, kStreamMessenger, cd.k0, cd.k1);
+        T g0, g1, g2, g3;
+        box_muller(w.x, w.y, g0, g1);
+        box_muller(w.z, w.w, g2, g3);
+        const cx<T> bc0 = ldc<T>(cd.bc + i0), bc1 = ldc<T>(cd.bc + i0 + 1);
+        const cx<T> bc2 = ldc<T>(cd.bc + i0 + 2), bc3 = ldc<T>(cd.bc + i0 + 3);
+        Z0[q].re = bc0.im + bc0.re * Z0[q].re + sqrt(tau * bc0.re) * g0;
+        Z0[q].im = bc1.im + bc1.re * Z0[q].im + sqrt(tau * bc1.re) * g1;
+        Z1[q].re = bc2.im + bc2.re * Z1[q].re + sqrt(tau * bc2.re) * g2;
+        Z1[q].im = bc3.im + bc3.re * Z1[q].im + sqrt(tau * bc3.re) * g3;
+      }
+    }
+    if constexpr (MODE != kModeMaterialize) {
+      Dft<Q2, -1, T>::run(Z0);
+      Dft<Q2, -1, T>::run(Z1);
+#pragma unroll
+      for (int v = 0; v < Q2; ++v) {
+        const cx<T> y0 = (pp * v == 0) ? Z0[v] : cmul(Z0[v], ldc<T>(tw + 2 * pp * v));
+        const cx<T> y1 = cmul(Z1[v], ldc<T>(tw + 2 * (pp + 1) * v));
+        stc<T>(row + pp * Q2 + v, y0);
+        stc<T>(row + (pp + 1) * Q2 + v, y1);
+      }
+    }
+  }
+  if constexpr (MODE == kModeMaterialize) return;
+  __syncthreads();
+
+  // Row stage F2 (per v2): DFT_P2 over p of column p*Q2 + v2 -> Z''[Q2 u + v2].
+  for (int it = threadIdx.x; it < ROWS * Q2; it += NT) {
+    const int r = it % ROWS;
+    const int v = it / ROWS;
+    V2* row = rows + r * RS;
+    cx<T> X[P2];
+#pragma unroll
+    for (int p = 0; p < P2; ++p) X[p] = ldc<T>(row + p * Q2 + v);
+    Dft<P2, -1, T>::run(X);
+#pragma unroll
+    for (int u = 0; u < P2; ++u) stc<T>(row + Q2 * u + v, X[u]);
+  }
+  __syncthreads();
+
+  // Row post-processing of the R2C z-transform:
+  // X[k] = (Z[k] + conj Z[H-k])/2 - i W_n^{k} (Z[k] - conj Z[H-k])/2, and the
+  // real X[0], X[n/2] packed as X[0] + i X[n/2].
+  for (int it = threadIdx.x; it < ROWS * (H / 2 + 1); it += NT) {
+    const int r = it % ROWS;
+    const int k = it / ROWS;
+    V2* row = rows + r * RS;
+    if (k == 0) {
+      const cx<T> z = ldc<T>(row);
+      stc<T>(row, cx<T>{z.re + z.im, z.re - z.im});
+    } else {
+      const int kk = H - k;
+      const cx<T> a = ldc<T>(row + k), b = ldc<T>(row + kk);
+      const T h = T(0.5);
+      {
+        const cx<T> e = cscale(cadd(a, cconj(b)), h), o = cscale(csub(a, cconj(b)), h);
+        stc<T>(row + k, cadd(e, cmul(cmul_i<-1>(o), ldc<T>(tw + k))));
+      }
+      if (kk != k) {
+        const cx<T> e = cscale(cadd(b, cconj(a)), h), o = cscale(csub(b, cconj(a)), h);
+        stc<T>(row + kk, cadd(e, cmul(cmul_i<-1>(o), ldc<T>(tw + kk))));
+      }
+    }
+  }
+  __syncthreads();
+
+  // Column stage F1 (per p of this CTA, local): DFT_Q over q of slot p*Q + q,
+  // twiddle W_N^{p v}, back to slot p*Q + v.
+  for (int it = threadIdx.x; it < H * PC; it += NT) {
+    const int l = it % H;
+    const int pl = it / H;
+    const int p = int(rank) * PC + pl;
+    cx<T> Z[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) Z[q] = ldc<T>(rows + (pl * Q + q) * RS + l);
+    Dft<Q, -1, T>::run(Z);
+#pragma unroll
+    for (int v = 0; v < Q; ++v) {
+      const cx<T> y = (p * v == 0) ? Z[v] : cmul(Z[v], ldc<T>(tw + p * v));
+      stc<T>(rows + (pl * Q + v) * RS + l, y);
+    }
+  }
+  cluster_barrier<C>();
+
+  // Column stage F2 (per v of this CTA): DFT_P over p of slot p*Q + v (any
+  // CTA) -> X[Q u + v] -> global; the packed column 0 goes to CTA 0's scratch.
+  for (int it = threadIdx.x; it < H * QC; it += NT) {
+    const int l = it % H;
+    const int v = int(rank) * QC + it / H;
+    cx<T> X[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) X[p] = ldc<T>(rbase[p / PC] + ((p % PC) * Q + v) * RS + l);
+    Dft<P, -1, T>::run(X);
+    if (l != 0) {
+#pragma unroll
+      for (int u = 0; u < P; ++u) stc<T>(mainp + size_t(Q * u + v) * H + l, X[u]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < P; ++u) stc<T>(col0_r0 + Q * u + v, X[u]);
+    }
+  }
+  cluster_barrier<C>();
+
+  // Unpack column 0: F = A + i B with A (kz = 0) and B (kz = n/2) Hermitian in ky.
+  if (rank == 0) {
+    for (int ky = threadIdx.x; ky < N; ky += NT) {
+      const cx<T> f = ldc<T>(col0 + ky);
+      const cx<T> g = cconj(ldc<T>(col0 + (N - ky) % N));
+      const T h = T(0.5);
+      stc<T>(mainp + size_t(ky) * H, cscale(cadd(f, g), h));
+      stc<T>(nyqp + ky, cmul_i<-1>(cscale(csub(f, g), h)));
+    }
+  }
+}
+
+}  // namespace mg

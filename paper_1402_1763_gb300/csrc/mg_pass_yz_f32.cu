@@ -1,0 +1,30 @@
+// Pass YZ instantiations, FP32.
+#include "mg_pass_yz_launch.cuh"
+
+namespace mg {
+
+template <>
+cudaError_t launch_pass_yz<float>(int n, int C, int mode, const ChainDev<float>* d, int nc, const uint32_t* sw,
+                                  const void* tw, cudaStream_t st) {
+  using namespace yzimpl;
+#define MG_CASE(N_, C_) \
+  if (n == N_ && C == C_) return run_mode<float, N_, C_>(mode, d, nc, sw, tw, st);
+  MG_CASE(8, 1)
+  MG_CASE(12, 1)
+  MG_CASE(16, 1)
+  MG_CASE(24, 1)
+  MG_CASE(32, 1)
+  MG_CASE(48, 1)
+  MG_CASE(64, 1)
+  MG_CASE(96, 1)
+  MG_CASE(128, 1)
+  MG_CASE(128, 2)
+  MG_CASE(192, 1)
+  MG_CASE(192, 2)
+  MG_CASE(256, 2)
+  MG_CASE(256, 4)
+#undef MG_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mg
