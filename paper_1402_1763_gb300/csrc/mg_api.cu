@@ -561,7 +561,7 @@ bool supported_n(int n) { return is_supported_n(n); }
 int yz_cluster_choices(int n, int precision, int* out, int max_out) {
   std::vector<int> v;
   if (precision == 32) {
-    if (n == 256) v = {2, 4};
+    if (n == 256) v = {4, 2};
     else if (n == 192) v = {1, 2};
     else if (n == 128) v = {1, 2};
     else v = {1};

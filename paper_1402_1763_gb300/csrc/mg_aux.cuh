@@ -78,7 +78,7 @@ __global__ void messenger_constants_kernel(const double* __restrict__ N, const d
 // InvGamma(n_b/2, sigma_b/2) from Jeffreys' prior (Sec. 3.2); P_b = (V/M) S_b.
 // Empty shells, and shells whose sums are not positive and finite (flagged),
 // keep their P.  Then a_b = S/(S + tau), sd_b = sqrt(S tau / (S + tau))
-// (Sec. 3.1), stored as (a_b / sqrt(M), sd_b) for pass X; the DC entry is 0.
+// (Sec. 3.1), stored as (a_b / M, sd_b / sqrt(M)) for pass X; the DC entry is 0.
 // draw = 0: only recompute the coefficients from P (set-up, mg_set_pk).
 // fix_P != 0: sum the shells but keep P (the signal sampler alone).
 template <typename T>
@@ -109,7 +109,7 @@ __global__ void shell_draw_kernel(const DrawDev* __restrict__ chains, int draw, 
   if (threadIdx.x != 0) return;
   double P = cd.P[b];
   if (draw) {
-    const double sig = r1[0], chi = r2[0];
+    const double sig = r1[0] * cd.M, chi = r2[0];  // pass X sums w |s_hat|^2 / M
     cd.sig_last[b] = sig;
     cd.chi_last[b] = chi;
     if (!fix_P && cd.n_b[b] > 0) {
@@ -126,8 +126,8 @@ __global__ void shell_draw_kernel(const DrawDev* __restrict__ chains, int draw, 
   const double sd = sqrt(Sh * cd.tau / (Sh + cd.tau));
   typename VT<T>::c2* coef = static_cast<typename VT<T>::c2*>(cd.coef);
   typename VT<T>::c2 v;
-  v.x = T(a / sqrt(cd.M));
-  v.y = T(sd);
+  v.x = T(a / cd.M);
+  v.y = T(sd / sqrt(cd.M));
   coef[b] = v;
   if (b == 0) {
     v.x = T(0);

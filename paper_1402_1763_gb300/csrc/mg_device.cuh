@@ -47,7 +47,7 @@ struct ChainDev {
   typename VT<T>::c2* main;
   typename VT<T>::c2* nyq;
   const typename VT<T>::c2* bc;
-  const typename VT<T>::c2* coef;  // [B+2]: (a / sqrt(M), sd) per shell; [B+1] = DC
+  const typename VT<T>::c2* coef;  // [B+2]: (a / M, sd / sqrt(M)) per shell; [B+1] = DC
   double* partial;                 // [tiles][B+1][2]: per-tile (sigma_b, X_b)
   const uint8_t* bin_of_m2;
   T* s_out;                        // real-space output of the materialise pass

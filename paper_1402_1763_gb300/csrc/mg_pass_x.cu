@@ -10,6 +10,12 @@ constexpr int pass_x_threads() {
   // threads per CTA: 32 pencils x (threads per pencil)
   return N >= 128 ? 256 : (N >= 32 ? 128 : 64);
 }
+// resident CTAs per SM the register budget is sized for (FP32 tiles are small
+// enough in shared memory for three)
+template <typename T, int N>
+constexpr int pass_x_minblocks() {
+  return (sizeof(T) == 4 && N >= 128) ? 3 : 1;
+}
 
 template <typename T, int N>
 cudaError_t run_x(const ChainDev<T>* d_chains, int n_chains, const uint32_t* d_sweep, const void* tw,
@@ -17,7 +23,7 @@ cudaError_t run_x(const ChainDev<T>* d_chains, int n_chains, const uint32_t* d_s
   constexpr int NT = pass_x_threads<N>();
   using S = PassXShape<T, N>;
   const size_t smem = S::smem_bytes(NT / 32, B_max);
-  auto kern = pass_x_kernel<T, N, NT>;
+  auto kern = pass_x_kernel<T, N, NT, pass_x_minblocks<T, N>()>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess || n_chains == 0) return e;  // n_chains == 0: set attributes only
   const unsigned grid = unsigned(S::kTiles) * unsigned(n_chains);

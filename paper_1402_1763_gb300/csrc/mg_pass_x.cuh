@@ -89,12 +89,13 @@ __device__ __forceinline__ void shell_accumulate(T v1, T v2, int bin, T* accw, i
 }
 
 // The signal draw of one stored mode (kx, ky, kz).  F is the unnormalised
-// forward DFT of t, i.e. sqrt(M) t_hat.  Returns s_hat / sqrt(M), the value the
-// unnormalised inverse transforms turn into s; reports the shell id (or -1) and
-// the mode's contributions w |s_hat|^2 and its w squared normals.
+// forward DFT of t, i.e. sqrt(M) t_hat.  With the shell's coefficients
+// (a/M, sd/sqrt(M)) the result is s_hat / sqrt(M), the value the unnormalised
+// inverse transforms turn into s.  Reports the shell id (or -1), w |s_hat|^2 / M
+// (the shell draw multiplies the sums by M) and the mode's w squared normals.
 template <typename T, int N>
 __device__ __forceinline__ cx<T> draw_mode(cx<T> F, int kx, int ky, int kz, bool valid,
-                                           const ChainDev<T>& cd, uint32_t sweep, T inv_sqrtM,
+                                           const ChainDev<T>& cd, uint32_t sweep,
                                            int& bin, T& sig, T& chi) {
   constexpr int H = N / 2;
   const int mx = kx <= H ? kx : kx - N;
@@ -103,17 +104,18 @@ __device__ __forceinline__ cx<T> draw_mode(cx<T> F, int kx, int ky, int kz, bool
   const uint32_t j = uint32_t((kx * N + ky) * (H + 1) + kz);
   const bool edge = (kz == 0) || (kz == H);
   const u32x4 w = philox4x32_10(j, sweep, cd.chain_id, kStreamModes, cd.k0, cd.k1);
-  T z0, z1, z2, z3;
-  box_muller(w.x, w.y, z0, z1);
-  box_muller(w.z, w.w, z2, z3);
+  T z0, z1;
+  normal_pair<T>(w.x, w.y, z0, z1);
   const T rs2 = T(0.70710678118654752440);
   cx<T> xi;
   T wgt;
   if (!edge) {
     xi = {z0 * rs2, z1 * rs2};
-    chi = z2 * z2 + z3 * z3;
+    chi = radius2<T>(w.z);  // z2^2 + z3^2 of the pair (w.z, w.w)
     wgt = T(2);
   } else {
+    T z2, z3;
+    normal_pair<T>(w.z, w.w, z2, z3);
     chi = z2 * z2;
     wgt = T(1);
     const uint32_t jp = uint32_t(((((N - kx) % N) * N) + ((N - ky) % N)) * (H + 1) + kz);
@@ -124,7 +126,7 @@ __device__ __forceinline__ cx<T> draw_mode(cx<T> F, int kx, int ky, int kz, bool
     } else {
       const u32x4 wp = philox4x32_10(jp, sweep, cd.chain_id, kStreamModes, cd.k0, cd.k1);
       T p0, p1;
-      box_muller(wp.x, wp.y, p0, p1);
+      normal_pair<T>(wp.x, wp.y, p0, p1);
       xi = {p0 * rs2, -(p1 * rs2)};
     }
   }
@@ -138,7 +140,7 @@ __device__ __forceinline__ cx<T> draw_mode(cx<T> F, int kx, int ky, int kz, bool
     sig = T(0);
     chi = T(0);
   }
-  return {s.re * inv_sqrtM, s.im * inv_sqrtM};
+  return s;
 }
 
 template <typename T, int N>
@@ -155,8 +157,8 @@ struct PassXShape {
   }
 };
 
-template <typename T, int N, int NT>
-__global__ void __launch_bounds__(NT) pass_x_kernel(const ChainDev<T>* __restrict__ chains,
+template <typename T, int N, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const ChainDev<T>* __restrict__ chains,
                                                     const uint32_t* __restrict__ sweep_ctr,
                                                     const typename VT<T>::c2* __restrict__ tw) {
   using S = PassXShape<T, N>;
@@ -174,7 +176,6 @@ __global__ void __launch_bounds__(NT) pass_x_kernel(const ChainDev<T>* __restric
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int B1 = cd.B + 1;
   const uint32_t sweep = *sweep_ctr;
-  const T inv_sqrtM = T(1.0 / sqrt(double(N) * double(N) * double(N)));
 
   for (int i = threadIdx.x; i < NW * B1 * Acc<T>::kWords; i += NT) acc[i] = T(0);
 
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(NT) pass_x_kernel(const ChainDev<T>* __restric
     for (int u = 0; u < P; ++u) {
       int bin;
       T sg, ch;
-      X[u] = draw_mode<T, N>(X[u], Q * u + vq, ky, kz, valid, cd, sweep, inv_sqrtM, bin, sg, ch);
+      X[u] = draw_mode<T, N>(X[u], Q * u + vq, ky, kz, valid, cd, sweep, bin, sg, ch);
       shell_accumulate<T>(sg, ch, bin, accw, lane);
     }
     Dft<P, +1, T>::run(X);

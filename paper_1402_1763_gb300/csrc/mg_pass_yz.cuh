@@ -51,8 +51,8 @@ __device__ __forceinline__ void cluster_barrier() {
   }
 }
 
-template <typename T, int N, int C, int MODE, int NT>
-__global__ void __launch_bounds__(NT) pass_yz_kernel(const ChainDev<T>* __restrict__ chains, int n_chains,
+template <typename T, int N, int C, int MODE, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const ChainDev<T>* __restrict__ chains, int n_chains,
                                                      const uint32_t* __restrict__ sweep_ctr,
                                                      const typename VT<T>::c2* __restrict__ tw) {
   using S = PassYZShape<T, N, C>;
@@ -201,14 +201,18 @@ __global__ void __launch_bounds__(NT) pass_yz_kernel(const ChainDev<T>* __restri
         o[2] = Z1[q].re;
         o[3] = Z1[q].im;
       } else if constexpr (MODE == kModeLoad) {
+        // The state holds the y/z transform of s divided by n^2, the form the
+        // x pass leaves behind (its inverse x transform is unnormalised and
+        // the unitary 1/sqrt(M) factors sit in the draw coefficients).
         const T* si = cd.s_in + i0;
-        Z0[q] = {si[0], si[1]};
-        Z1[q] = {si[2], si[3]};
+        const T sc = T(1.0 / (double(N) * double(N)));
+        Z0[q] = {si[0] * sc, si[1] * sc};
+        Z1[q] = {si[2] * sc, si[3] * sc};
       } else {
         const u32x4 w = philox4x32_10(uint32_t(i0 >> 2), sweep, cd.chain_id, kStreamMessenger, cd.k0, cd.k1);
         T g0, g1, g2, g3;
-        box_muller(w.x, w.y, g0, g1);
-        box_muller(w.z, w.w, g2, g3);
+        normal_pair<T>(w.x, w.y, g0, g1);
+        normal_pair<T>(w.z, w.w, g2, g3);
         const cx<T> bc0 = ldc<T>(cd.bc + i0), bc1 = ldc<T>(cd.bc + i0 + 1);
         const cx<T> bc2 = ldc<T>(cd.bc + i0 + 2), bc3 = ldc<T>(cd.bc + i0 + 3);
         Z0[q].re = bc0.im + bc0.re * Z0[q].re + sqrt(tau * bc0.re) * g0;

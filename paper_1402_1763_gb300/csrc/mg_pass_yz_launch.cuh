@@ -7,17 +7,23 @@
 namespace mg {
 namespace yzimpl {
 
-template <int N>
+// Threads per CTA and the resident CTAs per SM the register budget targets:
+// two CTAs per SM wherever two planes (or plane slices) fit in shared memory.
+template <typename T, int N, int C>
+constexpr int yz_minblocks() {
+  return 2 * PassYZShape<T, N, C>::kSmemBytes <= 220 * 1024 ? 2 : 1;
+}
+template <typename T, int N, int C>
 constexpr int yz_threads() {
-  return N >= 128 ? 512 : (N >= 48 ? 256 : 128);
+  return N < 48 ? 128 : (yz_minblocks<T, N, C>() == 2 ? 256 : 512);
 }
 
 template <typename T, int N, int C, int MODE>
 cudaError_t run(const ChainDev<T>* d_chains, int n_chains, const uint32_t* d_sweep, const void* tw,
                 cudaStream_t st) {
-  constexpr int NT = yz_threads<N>();
+  constexpr int NT = yz_threads<T, N, C>();
   using S = PassYZShape<T, N, C>;
-  auto kern = pass_yz_kernel<T, N, C, MODE, NT>;
+  auto kern = pass_yz_kernel<T, N, C, MODE, NT, yz_minblocks<T, N, C>()>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmemBytes));
   if (e != cudaSuccess || n_chains == 0) return e;  // n_chains == 0: set attributes only
   cudaLaunchConfig_t cfg = {};

@@ -59,6 +59,50 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& z0, 
   z1 = r * s;
 }
 
+// The FP32 path's Box-Muller on the special-function unit: U = fma(w, 2^-32,
+// 2^-33); -2 ln U from the hardware base-2 logarithm; the angle 2 pi U is
+// shifted by pi into (-pi, pi] so the hardware sine and cosine stay in their
+// accurate range (|error| <= 2^-21.4 there).  The normals agree with the FP64
+// construction to ~1e-6 absolute.
+__device__ __forceinline__ float u01_fast(uint32_t w) { return fmaf(__uint2float_rn(w), 0x1p-32f, 0x1p-33f); }
+
+__device__ __forceinline__ float minus2log_fast(uint32_t w) { return -1.3862943611198906f * __log2f(u01_fast(w)); }
+
+__device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float& z0, float& z1) {
+  const float r2 = minus2log_fast(wa);
+  const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+  float s, c;
+  __sincosf(6.28318530717958647692f * (u01_fast(wb) - 0.5f), &s, &c);
+  z0 = -(r * c);
+  z1 = -(r * s);
+}
+
+// Precision dispatch: FP64 uses the correctly rounded construction above, the
+// FP32 path the special-function-unit one.
+template <typename T>
+__device__ __forceinline__ void normal_pair(uint32_t wa, uint32_t wb, T& z0, T& z1);
+template <>
+__device__ __forceinline__ void normal_pair<double>(uint32_t wa, uint32_t wb, double& z0, double& z1) {
+  box_muller(wa, wb, z0, z1);
+}
+template <>
+__device__ __forceinline__ void normal_pair<float>(uint32_t wa, uint32_t wb, float& z0, float& z1) {
+  box_muller_fast(wa, wb, z0, z1);
+}
+
+// -2 ln U of one word: the squared radius of a Box-Muller pair, i.e. the sum
+// of the squares of the two normals the pair yields.
+template <typename T>
+__device__ __forceinline__ T radius2(uint32_t w);
+template <>
+__device__ __forceinline__ double radius2<double>(uint32_t w) {
+  return -2.0 * log((2.0 * double(w) + 1.0) * 0x1p-33);
+}
+template <>
+__device__ __forceinline__ float radius2<float>(uint32_t w) {
+  return minus2log_fast(w);
+}
+
 // Stream ids (counter word 3).
 constexpr uint32_t kStreamMessenger = 0;
 constexpr uint32_t kStreamModes = 1;
