@@ -54,7 +54,8 @@ struct SizeClass {
   int B_max = 0;
   std::vector<int> chains;         // context chain indices
   std::shared_ptr<DevBuf> d_desc;  // ChainDev<T>[chains.size()]
-  std::shared_ptr<DevBuf> tw;      // W_n^k, k < n, in the context precision
+  std::shared_ptr<DevBuf> tw;      // twiddle tables (TwLayout), context precision
+  std::vector<std::vector<char>> args;  // LaunchArgs<T> per chunk of <= kMaxLaunchChains chains
 };
 
 }  // namespace
@@ -152,14 +153,58 @@ std::vector<uint8_t> build_bin_table(int n, double L, int B, const double* edges
   return tab;
 }
 
+void split_of(int n, int* P, int* Q) {
+  switch (n) {
+#define MG_SPLIT_CASE(N_) \
+  case N_:                \
+    *P = Split<N_>::P;    \
+    *Q = Split<N_>::Q;    \
+    return;
+    MG_SPLIT_CASE(4)
+    MG_SPLIT_CASE(6)
+    MG_SPLIT_CASE(8)
+    MG_SPLIT_CASE(12)
+    MG_SPLIT_CASE(16)
+    MG_SPLIT_CASE(24)
+    MG_SPLIT_CASE(32)
+    MG_SPLIT_CASE(48)
+    MG_SPLIT_CASE(64)
+    MG_SPLIT_CASE(96)
+    MG_SPLIT_CASE(128)
+    MG_SPLIT_CASE(192)
+    MG_SPLIT_CASE(256)
+#undef MG_SPLIT_CASE
+    default:
+      *P = *Q = 0;
+  }
+}
+
+// Twiddle tables of grid size n in the layout of TwLayout (mg_device.cuh),
+// each value exp(-2 pi i e / n) evaluated in long double and rounded once.
 template <typename T>
 std::vector<typename VT<T>::c2> twiddles(int n) {
-  std::vector<typename VT<T>::c2> t(n);
-  for (int k = 0; k < n; ++k) {
-    const long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)k / (long double)n;
-    t[k].x = T(std::cos(a));
-    t[k].y = T(std::sin(a));
-  }
+  int P, Q, P2, Q2;
+  split_of(n, &P, &Q);
+  split_of(n / 2, &P2, &Q2);
+  std::vector<typename VT<T>::c2> t(size_t(4) * n);
+  auto W = [n](long e) {
+    const long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)(e % n) / (long double)n;
+    typename VT<T>::c2 v;
+    v.x = T(std::cos(a));
+    v.y = T(std::sin(a));
+    return v;
+  };
+  for (int k = 0; k < n; ++k) t[k] = W(k);
+  for (int v = 0; v < Q; ++v)
+    for (int p = 0; p < P; ++p) {
+      t[n + v * P + p] = W(long(p) * v);
+      t[2 * n + p * Q + v] = W(long(p) * v);
+    }
+  for (int v = 0; v < Q2; ++v)
+    for (int p = 0; p < P2; ++p) {
+      t[3 * n + v * P2 + p] = W(2L * p * v);
+      t[3 * n + n / 2 + p * Q2 + v] = W(2L * p * v);
+    }
   return t;
 }
 
@@ -181,9 +226,6 @@ mg_status upload_descriptors(mg_ctx* c) {
       d.s_out = nullptr;
       d.s_in = nullptr;
       d.tau = T(g.tau);
-      d.k0 = uint32_t(g.seed & 0xffffffffu);
-      d.k1 = uint32_t(g.seed >> 32);
-      d.chain_id = ch.chain_id;
       d.B = g.B;
     }
     cudaError_t e;
@@ -194,6 +236,23 @@ mg_status upload_descriptors(mg_ctx* c) {
     sc.tw = dalloc(tw.size() * sizeof(V2), &e);
     MG_CUDA(c, e);
     MG_CUDA(c, cudaMemcpy(sc.tw->p, tw.data(), tw.size() * sizeof(V2), cudaMemcpyHostToDevice));
+    sc.args.clear();
+    for (size_t c0 = 0; c0 < sc.chains.size(); c0 += kMaxLaunchChains) {
+      LaunchArgs<T> a;
+      std::memset(&a, 0, sizeof(a));
+      a.chains = static_cast<const ChainDev<T>*>(sc.d_desc->p) + c0;
+      a.sweep_ctr = static_cast<const uint32_t*>(c->d_sweep->p);
+      a.tw = static_cast<const V2*>(sc.tw->p);
+      a.n_chains = int(std::min<size_t>(kMaxLaunchChains, sc.chains.size() - c0));
+      for (int k = 0; k < a.n_chains; ++k) {
+        const Chain& ch = c->chains[sc.chains[c0 + k]];
+        const Group& g = c->groups[ch.group];
+        a.k0[k] = uint32_t(g.seed & 0xffffffffu);
+        a.k1[k] = uint32_t(g.seed >> 32);
+        a.cid[k] = ch.chain_id;
+      }
+      sc.args.emplace_back(reinterpret_cast<const char*>(&a), reinterpret_cast<const char*>(&a) + sizeof(a));
+    }
   }
   std::vector<DrawDev> dd(c->chains.size());
   for (size_t i = 0; i < c->chains.size(); ++i) {
@@ -233,17 +292,16 @@ mg_status launch_shell_draw(mg_ctx* c, int draw, bool count_sweep) {
 template <typename T>
 mg_status enqueue_passes(mg_ctx* c, int which) {
   const uint32_t* sw = static_cast<const uint32_t*>(c->d_sweep->p);
+  (void)sw;
   if (which & 1) {
-    for (auto& sc : c->classes) {
-      MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, 0, static_cast<const ChainDev<T>*>(sc.d_desc->p),
-                                   int(sc.chains.size()), sw, sc.tw->p, c->stream));
-    }
+    for (auto& sc : c->classes)
+      for (auto& blob : sc.args)
+        MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, 0, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()), c->stream));
   }
   if (which & 2) {
-    for (auto& sc : c->classes) {
-      MG_CUDA(c, launch_pass_x<T>(sc.n, static_cast<const ChainDev<T>*>(sc.d_desc->p), int(sc.chains.size()), sw,
-                                  sc.tw->p, sc.B_max, c->stream));
-    }
+    for (auto& sc : c->classes)
+      for (auto& blob : sc.args)
+        MG_CUDA(c, launch_pass_x<T>(sc.n, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()), sc.B_max, c->stream));
   }
   if (which & 4) return launch_shell_draw<T>(c, 1, true);
   return MG_OK;
@@ -253,10 +311,10 @@ mg_status enqueue_sweep(mg_ctx* c) {
   return c->precision == 32 ? enqueue_passes<float>(c, 7) : enqueue_passes<double>(c, 7);
 }
 
-// One chain's descriptor with an input or output field pointer attached.
+// Launch arguments for one chain with an input or output field pointer attached.
 template <typename T>
-mg_status single_chain_desc(mg_ctx* c, int chain, T* s_out, const T* s_in, SizeClass** sc_out,
-                            std::shared_ptr<DevBuf>* desc) {
+mg_status single_chain_args(mg_ctx* c, int chain, T* s_out, const T* s_in, SizeClass** sc_out,
+                            std::shared_ptr<DevBuf>* desc, LaunchArgs<T>* args) {
   for (auto& sc : c->classes) {
     for (size_t i = 0; i < sc.chains.size(); ++i) {
       if (sc.chains[i] != chain) continue;
@@ -269,6 +327,15 @@ mg_status single_chain_desc(mg_ctx* c, int chain, T* s_out, const T* s_in, SizeC
       MG_CUDA(c, e);
       MG_CUDA(c, cudaMemcpyAsync((*desc)->p, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
       MG_CUDA(c, cudaStreamSynchronize(c->stream));
+      const LaunchArgs<T>& src = *reinterpret_cast<const LaunchArgs<T>*>(sc.args[i / kMaxLaunchChains].data());
+      std::memset(args, 0, sizeof(*args));
+      args->chains = static_cast<const ChainDev<T>*>((*desc)->p);
+      args->sweep_ctr = src.sweep_ctr;
+      args->tw = src.tw;
+      args->n_chains = 1;
+      args->k0[0] = src.k0[i % kMaxLaunchChains];
+      args->k1[0] = src.k1[i % kMaxLaunchChains];
+      args->cid[0] = src.cid[i % kMaxLaunchChains];
       *sc_out = &sc;
       return MG_OK;
     }
@@ -280,10 +347,10 @@ template <typename T>
 mg_status materialize(mg_ctx* c, int chain, T* out_dev) {
   SizeClass* sc;
   std::shared_ptr<DevBuf> desc;
-  mg_status s = single_chain_desc<T>(c, chain, out_dev, nullptr, &sc, &desc);
+  LaunchArgs<T> a;
+  mg_status s = single_chain_args<T>(c, chain, out_dev, nullptr, &sc, &desc, &a);
   if (s != MG_OK) return s;
-  MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, 1, static_cast<const ChainDev<T>*>(desc->p), 1,
-                               static_cast<const uint32_t*>(c->d_sweep->p), sc->tw->p, c->stream));
+  MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, 1, a, c->stream));
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
   return MG_OK;
 }
@@ -292,10 +359,10 @@ template <typename T>
 mg_status load_s(mg_ctx* c, int chain, const T* in_dev) {
   SizeClass* sc;
   std::shared_ptr<DevBuf> desc;
-  mg_status s = single_chain_desc<T>(c, chain, nullptr, in_dev, &sc, &desc);
+  LaunchArgs<T> a;
+  mg_status s = single_chain_args<T>(c, chain, nullptr, in_dev, &sc, &desc, &a);
   if (s != MG_OK) return s;
-  MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, 2, static_cast<const ChainDev<T>*>(desc->p), 1,
-                               static_cast<const uint32_t*>(c->d_sweep->p), sc->tw->p, c->stream));
+  MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, 2, a, c->stream));
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
   return MG_OK;
 }
@@ -320,10 +387,10 @@ mg_status record_stats(mg_ctx* c) {
     T* s = static_cast<T*>(c->d_scratch_s->p);
     SizeClass* sc;
     std::shared_ptr<DevBuf> desc;
-    mg_status st = single_chain_desc<T>(c, int(ci), s, nullptr, &sc, &desc);
+    LaunchArgs<T> a;
+    mg_status st = single_chain_args<T>(c, int(ci), s, nullptr, &sc, &desc, &a);
     if (st != MG_OK) return st;
-    MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, 1, static_cast<const ChainDev<T>*>(desc->p), 1,
-                                 static_cast<const uint32_t*>(c->d_sweep->p), sc->tw->p, c->stream));
+    MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, 1, a, c->stream));
     welford_kernel<T><<<1024, 256, 0, c->stream>>>(s, static_cast<double*>(c->chains[ci].mean->p),
                                                    static_cast<double*>(c->chains[ci].m2->p), g.M, inv);
     MG_CUDA(c, cudaGetLastError());
@@ -486,9 +553,10 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
   mg_status s = upload_descriptors<T>(c);
   if (s != MG_OK) return s;
   for (auto& sc : c->classes) {
-    for (int mode = 0; mode < 3; ++mode)
-      MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, mode, nullptr, 0, nullptr, nullptr, c->stream));
-    MG_CUDA(c, launch_pass_x<T>(sc.n, nullptr, 0, nullptr, nullptr, sc.B_max, c->stream));
+    LaunchArgs<T> none;
+    std::memset(&none, 0, sizeof(none));  // n_chains = 0: set kernel attributes only
+    for (int mode = 0; mode < 3; ++mode) MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, mode, none, c->stream));
+    MG_CUDA(c, launch_pass_x<T>(sc.n, none, sc.B_max, c->stream));
   }
   s = launch_shell_draw<T>(c, 0, false);
   if (s != MG_OK) return s;

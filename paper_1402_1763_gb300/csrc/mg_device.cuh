@@ -53,9 +53,57 @@ struct ChainDev {
   T* s_out;                        // real-space output of the materialise pass
   const T* s_in;                   // real-space input of the load pass
   T tau;
-  uint32_t k0, k1, chain_id;
   int B;
 };
+
+// Kernel parameters of one pass launch.  The Philox keys and chain ids sit in
+// the parameter space so every CTA reads them with a uniform index; a launch
+// covers at most kMaxLaunchChains chains (the host splits larger batches).
+constexpr int kMaxLaunchChains = 64;
+template <typename T>
+struct LaunchArgs {
+  const ChainDev<T>* chains;
+  const uint32_t* sweep_ctr;
+  const typename VT<T>::c2* tw;  // twiddle tables of this grid size (TwLayout)
+  int n_chains;
+  uint32_t k0[kMaxLaunchChains];
+  uint32_t k1[kMaxLaunchChains];
+  uint32_t cid[kMaxLaunchChains];
+};
+
+// Twiddle tables of one grid size n = P Q (rows of length n/2 = P2 Q2), all
+// W_n^e = exp(-2 pi i e / n), laid out so that a stage reads the twiddles it
+// needs as one contiguous row:
+//   lin[k]      W_n^k,        k < n
+//   cvp[v][p]   W_n^{p v},    v < Q, p < P    (column/x stages looping over v)
+//   cpv[p][v]   W_n^{p v},    p < P, v < Q    (column/x stages looping over p)
+//   rvp[v][p]   W_n^{2 p v},  v < Q2, p < P2  (row stages looping over v)
+//   rpv[p][v]   W_n^{2 p v},  p < P2, v < Q2  (row stages looping over p)
+template <int N>
+struct TwLayout {
+  static constexpr int kLin = 0, kCvp = N, kCpv = 2 * N, kRvp = 3 * N, kRpv = 3 * N + N / 2;
+  static constexpr int kSize = 4 * N;
+};
+
+// Load K consecutive complex twiddles (16-byte vector loads where aligned).
+template <typename T, int K>
+__device__ __forceinline__ void ld_tw_row(const typename VT<T>::c2* __restrict__ row, cx<T>* w) {
+  if constexpr (sizeof(T) == 4 && K % 2 == 0) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+    for (int i = 0; i < K / 2; ++i) {
+      const float4 q = __ldg(r4 + i);
+      w[2 * i] = {q.x, q.y};
+      w[2 * i + 1] = {q.z, q.w};
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const typename VT<T>::c2 q = __ldg(row + i);
+      w[i] = {q.x, q.y};
+    }
+  }
+}
 
 // What the P-draw kernel needs per chain.
 struct DrawDev {

@@ -18,12 +18,10 @@ size_t yz_smem_bytes(int n, int C, int precision);
 // n_chains == 0 only sets the kernels' attributes (done once, outside any
 // stream capture).
 template <typename T>
-cudaError_t launch_pass_yz(int n, int C, int mode, const ChainDev<T>* d_chains, int n_chains,
-                           const uint32_t* d_sweep, const void* tw, cudaStream_t st);
+cudaError_t launch_pass_yz(int n, int C, int mode, const LaunchArgs<T>& args, cudaStream_t st);
 
 int pass_x_tiles(int n);
 template <typename T>
-cudaError_t launch_pass_x(int n, const ChainDev<T>* d_chains, int n_chains, const uint32_t* d_sweep,
-                          const void* tw, int B_max, cudaStream_t st);
+cudaError_t launch_pass_x(int n, const LaunchArgs<T>& args, int B_max, cudaStream_t st);
 
 }  // namespace mg

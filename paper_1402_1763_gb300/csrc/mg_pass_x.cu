@@ -18,8 +18,8 @@ constexpr int pass_x_minblocks() {
 }
 
 template <typename T, int N>
-cudaError_t run_x(const ChainDev<T>* d_chains, int n_chains, const uint32_t* d_sweep, const void* tw,
-                  int B_max, cudaStream_t st) {
+cudaError_t run_x(const LaunchArgs<T>& args, int B_max, cudaStream_t st) {
+  const int n_chains = args.n_chains;
   constexpr int NT = pass_x_threads<N>();
   using S = PassXShape<T, N>;
   const size_t smem = S::smem_bytes(NT / 32, B_max);
@@ -27,7 +27,7 @@ cudaError_t run_x(const ChainDev<T>* d_chains, int n_chains, const uint32_t* d_s
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess || n_chains == 0) return e;  // n_chains == 0: set attributes only
   const unsigned grid = unsigned(S::kTiles) * unsigned(n_chains);
-  kern<<<grid, NT, smem, st>>>(d_chains, d_sweep, static_cast<const typename VT<T>::c2*>(tw));
+  kern<<<grid, NT, smem, st>>>(args);
   return cudaGetLastError();
 }
 }  // namespace
@@ -38,12 +38,11 @@ int pass_x_tiles(int n) {
 }
 
 template <typename T>
-cudaError_t launch_pass_x(int n, const ChainDev<T>* d_chains, int n_chains, const uint32_t* d_sweep,
-                          const void* tw, int B_max, cudaStream_t st) {
+cudaError_t launch_pass_x(int n, const LaunchArgs<T>& args, int B_max, cudaStream_t st) {
   switch (n) {
 #define MG_CASE(N_) \
   case N_:          \
-    return run_x<T, N_>(d_chains, n_chains, d_sweep, tw, B_max, st);
+    return run_x<T, N_>(args, B_max, st);
     MG_CASE(8)
     MG_CASE(12)
     MG_CASE(16)
@@ -61,9 +60,7 @@ cudaError_t launch_pass_x(int n, const ChainDev<T>* d_chains, int n_chains, cons
   }
 }
 
-template cudaError_t launch_pass_x<float>(int, const ChainDev<float>*, int, const uint32_t*, const void*, int,
-                                          cudaStream_t);
-template cudaError_t launch_pass_x<double>(int, const ChainDev<double>*, int, const uint32_t*, const void*, int,
-                                           cudaStream_t);
+template cudaError_t launch_pass_x<float>(int, const LaunchArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_pass_x<double>(int, const LaunchArgs<double>&, int, cudaStream_t);
 
 }  // namespace mg

@@ -53,13 +53,18 @@ struct Acc<double> {
 
 // Segmented warp reduction of (v1, v2) over runs of equal shell id, then the
 // head of each run adds the run's sums to this warp's accumulators.  bin < 0
-// marks lanes that contribute nothing.
+// marks lanes that contribute nothing.  When the shell ids do not decrease
+// along the warp (always the case for pencils of consecutive kz at one
+// (kx, ky)) the run heads hold distinct shells and update in parallel;
+// otherwise they update one after another in lane order.  Both orders are
+// fixed, so the sums are deterministic.
 template <typename T>
 __device__ __forceinline__ void shell_accumulate(T v1, T v2, int bin, T* accw, int lane) {
   const unsigned full = 0xffffffffu;
   const int prevb = __shfl_up_sync(full, bin, 1);
   const bool head = (lane == 0) || (prevb != bin);
   const unsigned heads = __ballot_sync(full, head);
+  const bool monotone = __all_sync(full, lane == 0 || prevb <= bin);
   const unsigned later = (lane == 31) ? 0u : (heads & (full << (lane + 1)));
   const int run_end = later ? (__ffs(later) - 2) : 31;
 #pragma unroll
@@ -72,10 +77,7 @@ __device__ __forceinline__ void shell_accumulate(T v1, T v2, int bin, T* accw, i
     }
   }
   const bool writer = head && bin >= 0;
-  const int key = writer ? bin : (-1000 - lane);
-  const unsigned same = __match_any_sync(full, key);
-  const bool dup = writer && (__popc(same) > 1);
-  if (!__any_sync(full, dup)) {
+  if (monotone) {
     if (writer) Acc<T>::add(accw + bin * Acc<T>::kWords, v1, v2);
   } else {
     unsigned hm = __ballot_sync(full, writer);
@@ -95,15 +97,15 @@ __device__ __forceinline__ void shell_accumulate(T v1, T v2, int bin, T* accw, i
 // (the shell draw multiplies the sums by M) and the mode's w squared normals.
 template <typename T, int N>
 __device__ __forceinline__ cx<T> draw_mode(cx<T> F, int kx, int ky, int kz, bool valid,
-                                           const ChainDev<T>& cd, uint32_t sweep,
-                                           int& bin, T& sig, T& chi) {
+                                           const ChainDev<T>& cd, uint32_t sweep, uint32_t k0, uint32_t k1,
+                                           uint32_t cid, int& bin, T& sig, T& chi) {
   constexpr int H = N / 2;
   const int mx = kx <= H ? kx : kx - N;
   const int my = ky <= H ? ky : ky - N;
   const int m2 = mx * mx + my * my + kz * kz;
   const uint32_t j = uint32_t((kx * N + ky) * (H + 1) + kz);
   const bool edge = (kz == 0) || (kz == H);
-  const u32x4 w = philox4x32_10(j, sweep, cd.chain_id, kStreamModes, cd.k0, cd.k1);
+  const u32x4 w = philox4x32_10(j, sweep, cid, kStreamModes, k0, k1);
   T z0, z1;
   normal_pair<T>(w.x, w.y, z0, z1);
   const T rs2 = T(0.70710678118654752440);
@@ -124,7 +126,7 @@ __device__ __forceinline__ cx<T> draw_mode(cx<T> F, int kx, int ky, int kz, bool
     } else if (j < jp) {
       xi = {z0 * rs2, z1 * rs2};
     } else {
-      const u32x4 wp = philox4x32_10(jp, sweep, cd.chain_id, kStreamModes, cd.k0, cd.k1);
+      const u32x4 wp = philox4x32_10(jp, sweep, cid, kStreamModes, k0, k1);
       T p0, p1;
       normal_pair<T>(wp.x, wp.y, p0, p1);
       xi = {p0 * rs2, -(p1 * rs2)};
@@ -158,11 +160,10 @@ struct PassXShape {
 };
 
 template <typename T, int N, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const ChainDev<T>* __restrict__ chains,
-                                                    const uint32_t* __restrict__ sweep_ctr,
-                                                    const typename VT<T>::c2* __restrict__ tw) {
+__global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const __grid_constant__ LaunchArgs<T> a) {
   using S = PassXShape<T, N>;
   using V2 = typename VT<T>::c2;
+  using TL = TwLayout<N>;
   constexpr int H = S::H, P = S::P, Q = S::Q, LW = S::LW;
   constexpr int NW = NT / 32;
   static_assert(NT % 32 == 0, "whole warps");
@@ -172,10 +173,11 @@ __global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const ChainDev<T>* __r
 
   const int tile = blockIdx.x % S::kTiles;
   const int chain = blockIdx.x / S::kTiles;
-  const ChainDev<T> cd = chains[chain];
+  const ChainDev<T> cd = a.chains[chain];
+  const uint32_t k0 = a.k0[chain], k1 = a.k1[chain], cid = a.cid[chain];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int B1 = cd.B + 1;
-  const uint32_t sweep = *sweep_ctr;
+  const uint32_t sweep = *a.sweep_ctr;
 
   for (int i = threadIdx.x; i < NW * B1 * Acc<T>::kWords; i += NT) acc[i] = T(0);
 
@@ -207,15 +209,16 @@ __global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const ChainDev<T>* __r
 #pragma unroll
     for (int q = 0; q < Q; ++q) v[q] = valid ? ldc<T>(base + size_t(p + P * q) * stride) : cx<T>{T(0), T(0)};
     Dft<Q, -1, T>::run(v);
+    cx<T> w[Q];
+    ld_tw_row<T, Q>(a.tw + TL::kCpv + p * Q, w);
 #pragma unroll
-    for (int vq = 0; vq < Q; ++vq) {
-      const cx<T> y = vq == 0 ? v[vq] : cmul(v[vq], ldc<T>(tw + p * vq));
-      stc<T>(xs + (p * Q + vq) * LW + lane, y);
-    }
+    for (int vq = 0; vq < Q; ++vq) stc<T>(xs + (p * Q + vq) * LW + lane, vq == 0 ? v[vq] : cmul(v[vq], w[vq]));
   }
   __syncthreads();
 
   // Stage F2 + draw + inverse stage I1, in place in the slots of column v.
+  // The modes kx = Q u + v pass through their shared-memory slots u*Q + v so
+  // that the draw runs as one compact (not unrolled) loop over u.
   T* accw = acc + warp * B1 * Acc<T>::kWords;
   for (int it = threadIdx.x; it < LW * Q; it += NT) {
     const int vq = it / LW;
@@ -224,18 +227,23 @@ __global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const ChainDev<T>* __r
     for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs + (p * Q + vq) * LW + lane);
     Dft<P, -1, T>::run(X);
 #pragma unroll
+    for (int u = 0; u < P; ++u) stc<T>(xs + (u * Q + vq) * LW + lane, X[u]);
+#pragma unroll 1
     for (int u = 0; u < P; ++u) {
+      V2* slot = xs + (u * Q + vq) * LW + lane;
       int bin;
       T sg, ch;
-      X[u] = draw_mode<T, N>(X[u], Q * u + vq, ky, kz, valid, cd, sweep, bin, sg, ch);
+      const cx<T> y = draw_mode<T, N>(ldc<T>(slot), Q * u + vq, ky, kz, valid, cd, sweep, k0, k1, cid, bin, sg, ch);
+      stc<T>(slot, y);
       shell_accumulate<T>(sg, ch, bin, accw, lane);
     }
-    Dft<P, +1, T>::run(X);
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-      const cx<T> y = (p * vq == 0) ? X[p] : cmulc(X[p], ldc<T>(tw + p * vq));
-      stc<T>(xs + (p * Q + vq) * LW + lane, y);
-    }
+    for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs + (p * Q + vq) * LW + lane);
+    Dft<P, +1, T>::run(X);
+    cx<T> w[P];
+    ld_tw_row<T, P>(a.tw + TL::kCvp + vq * P, w);
+#pragma unroll
+    for (int p = 0; p < P; ++p) stc<T>(xs + (p * Q + vq) * LW + lane, p == 0 ? X[p] : cmulc(X[p], w[p]));
   }
   __syncthreads();
 
@@ -258,20 +266,20 @@ __global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const ChainDev<T>* __r
     if constexpr (sizeof(T) == 4) {
       float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
       for (int w2 = 0; w2 < NW; ++w2) {
-        const float* a = acc + (w2 * B1 + b) * 4;
-        Acc<float>::two_sum(h1, l1, a[0]);
-        l1 += a[1];
-        Acc<float>::two_sum(h2, l2, a[2]);
-        l2 += a[3];
+        const float* ac = acc + (w2 * B1 + b) * 4;
+        Acc<float>::two_sum(h1, l1, ac[0]);
+        l1 += ac[1];
+        Acc<float>::two_sum(h2, l2, ac[2]);
+        l2 += ac[3];
       }
       part[2 * b + 0] = double(h1) + double(l1);
       part[2 * b + 1] = double(h2) + double(l2);
     } else {
       double s1 = 0.0, s2 = 0.0;
       for (int w2 = 0; w2 < NW; ++w2) {
-        const double* a = acc + (w2 * B1 + b) * 2;
-        s1 += a[0];
-        s2 += a[1];
+        const double* ac = acc + (w2 * B1 + b) * 2;
+        s1 += ac[0];
+        s2 += ac[1];
       }
       part[2 * b + 0] = s1;
       part[2 * b + 1] = s2;

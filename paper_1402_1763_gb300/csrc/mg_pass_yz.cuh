@@ -42,6 +42,33 @@ struct PassYZShape {
   static constexpr size_t kSmemBytes = (size_t(ROWS) * RS + N) * sizeof(typename VT<T>::c2);
 };
 
+// Distributed shared memory through 32-bit shared::cluster addresses: mapa
+// turns this CTA's shared address into the same offset in CTA `rank`.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_dsmem(uint32_t addr, cx<float> v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.re), "f"(v.im) : "memory");
+}
+__device__ __forceinline__ void st_dsmem(uint32_t addr, cx<double> v) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(addr), "d"(v.re), "d"(v.im) : "memory");
+}
+__device__ __forceinline__ cx<float> ld_dsmem(uint32_t addr, float) {
+  cx<float> v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.re), "=f"(v.im) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ cx<double> ld_dsmem(uint32_t addr, double) {
+  cx<double> v;
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.re), "=d"(v.im) : "r"(addr) : "memory");
+  return v;
+}
+
 template <int C>
 __device__ __forceinline__ void cluster_barrier() {
   if constexpr (C == 1) {
@@ -52,11 +79,11 @@ __device__ __forceinline__ void cluster_barrier() {
 }
 
 template <typename T, int N, int C, int MODE, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const ChainDev<T>* __restrict__ chains, int n_chains,
-                                                     const uint32_t* __restrict__ sweep_ctr,
-                                                     const typename VT<T>::c2* __restrict__ tw) {
+__global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const __grid_constant__ LaunchArgs<T> a) {
   using S = PassYZShape<T, N, C>;
   using V2 = typename VT<T>::c2;
+  using TL = TwLayout<N>;
+  const typename VT<T>::c2* __restrict__ tw = a.tw;
   constexpr int H = S::H, P = S::P, Q = S::Q, P2 = S::P2, Q2 = S::Q2;
   constexpr int ROWS = S::ROWS, RS = S::RS, PC = S::PC, QC = S::QC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -64,25 +91,23 @@ __global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const ChainDev<T>* __
   V2* col0 = rows + ROWS * RS;
 
   unsigned rank = 0;
-  V2* rbase[C];
-  V2* col0_r0;
-  if constexpr (C == 1) {
-    rbase[0] = rows;
-    col0_r0 = col0;
-  } else {
-    cg::cluster_group cl = cg::this_cluster();
-    rank = cl.block_rank();
+  uint32_t rbase[C];  // shared::cluster address of each CTA's rows (C > 1)
+  uint32_t col0_r0 = 0;
+  if constexpr (C > 1) {
+    rank = cg::this_cluster().block_rank();
 #pragma unroll
-    for (int r = 0; r < C; ++r) rbase[r] = cl.map_shared_rank(rows, r);
-    col0_r0 = cl.map_shared_rank(col0, 0);
+    for (int r = 0; r < C; ++r) rbase[r] = map_to_rank(smem_addr(rows), uint32_t(r));
+    col0_r0 = map_to_rank(smem_addr(col0), 0u);
   }
+  constexpr uint32_t kEl = sizeof(V2);
   const int unit = blockIdx.x / C;
-  const int x = unit / n_chains;
-  const int chain = unit % n_chains;
-  const ChainDev<T> cd = chains[chain];
+  const int x = unit / a.n_chains;
+  const int chain = unit % a.n_chains;
+  const ChainDev<T> cd = a.chains[chain];
+  const uint32_t k0 = a.k0[chain], k1 = a.k1[chain], cid = a.cid[chain];
   V2* mainp = cd.main + size_t(x) * N * H;
   V2* nyqp = cd.nyq + size_t(x) * N;
-  const uint32_t sweep = *sweep_ctr;
+  const uint32_t sweep = *a.sweep_ctr;
   const T tau = cd.tau;
 
   if constexpr (C > 1) cluster_barrier<C>();  // every CTA of the cluster is running
@@ -90,25 +115,45 @@ __global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const ChainDev<T>* __
   if constexpr (MODE != kModeLoad) {
     // Column stage I1 (per v of this CTA): IDFT_P over u of X[Q u + v] from
     // global, twiddle W_N^{-p v}, to slot p*Q + v (whichever CTA owns it).
-    for (int it = threadIdx.x; it < H * QC; it += NT) {
-      const int l = it % H;
-      const int v = int(rank) * QC + it / H;
-      cx<T> X[P];
+    // A thread issues the loads of BI items before transforming any of them.
+    constexpr int TI1 = H * QC;
+    constexpr int BI = TI1 >= 2 * NT ? 2 : 1;
+    for (int it0 = threadIdx.x; it0 < TI1; it0 += BI * NT) {
+      cx<T> X[BI][P];
 #pragma unroll
-      for (int u = 0; u < P; ++u) X[u] = ldc<T>(mainp + size_t(Q * u + v) * H + l);
-      if (l == 0) {
+      for (int b = 0; b < BI; ++b) {
+        const int it = it0 + b * NT;
+        if (it < TI1) {
+          const int l = it % H;
+          const int v = int(rank) * QC + it / H;
 #pragma unroll
-        for (int u = 0; u < P; ++u) {
-          const cx<T> b = ldc<T>(nyqp + Q * u + v);
-          X[u] = {X[u].re - b.im, X[u].im + b.re};
+          for (int u = 0; u < P; ++u) X[b][u] = ldc<T>(mainp + size_t(Q * u + v) * H + l);
+          if (l == 0) {
+#pragma unroll
+            for (int u = 0; u < P; ++u) {
+              const cx<T> y = ldc<T>(nyqp + Q * u + v);
+              X[b][u] = {X[b][u].re - y.im, X[b][u].im + y.re};
+            }
+          }
         }
       }
-      Dft<P, +1, T>::run(X);
 #pragma unroll
-      for (int p = 0; p < P; ++p) {
-        const cx<T> y = (p * v == 0) ? X[p] : cmulc(X[p], ldc<T>(tw + p * v));
-        // slot p*Q + v lives in CTA p / PC at local row (p % PC)*Q + v
-        stc<T>(rbase[p / PC] + ((p % PC) * Q + v) * RS + l, y);
+      for (int b = 0; b < BI; ++b) {
+        const int it = it0 + b * NT;
+        if (it >= TI1) continue;
+        const int l = it % H;
+        const int v = int(rank) * QC + it / H;
+        Dft<P, +1, T>::run(X[b]);
+        cx<T> w[P];
+        ld_tw_row<T, P>(tw + TL::kCvp + v * P, w);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const cx<T> y = p == 0 ? X[b][p] : cmulc(X[b][p], w[p]);
+          // slot p*Q + v lives in CTA p / PC at local row (p % PC)*Q + v
+          const int off = ((p % PC) * Q + v) * RS + l;
+          if constexpr (C == 1) stc<T>(rows + off, y);
+          else st_dsmem(rbase[p / PC] + uint32_t(off) * kEl, y);
+        }
       }
     }
     cluster_barrier<C>();
@@ -161,11 +206,10 @@ __global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const ChainDev<T>* __
 #pragma unroll
       for (int u = 0; u < P2; ++u) X[u] = ldc<T>(row + Q2 * u + v);
       Dft<P2, +1, T>::run(X);
+      cx<T> w[P2];
+      ld_tw_row<T, P2>(tw + TL::kRvp + v * P2, w);
 #pragma unroll
-      for (int p = 0; p < P2; ++p) {
-        const cx<T> y = (p * v == 0) ? X[p] : cmulc(X[p], ldc<T>(tw + 2 * p * v));
-        stc<T>(row + p * Q2 + v, y);
-      }
+      for (int p = 0; p < P2; ++p) stc<T>(row + p * Q2 + v, p == 0 ? X[p] : cmulc(X[p], w[p]));
     }
     __syncthreads();
   }
@@ -209,12 +253,13 @@ __global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const ChainDev<T>* __
         Z0[q] = {si[0] * sc, si[1] * sc};
         Z1[q] = {si[2] * sc, si[3] * sc};
       } else {
-        const u32x4 w = philox4x32_10(uint32_t(i0 >> 2), sweep, cd.chain_id, kStreamMessenger, cd.k0, cd.k1);
+        const u32x4 w = philox4x32_10(uint32_t(i0 >> 2), sweep, cid, kStreamMessenger, k0, k1);
         T g0, g1, g2, g3;
         normal_pair<T>(w.x, w.y, g0, g1);
         normal_pair<T>(w.z, w.w, g2, g3);
-        const cx<T> bc0 = ldc<T>(cd.bc + i0), bc1 = ldc<T>(cd.bc + i0 + 1);
-        const cx<T> bc2 = ldc<T>(cd.bc + i0 + 2), bc3 = ldc<T>(cd.bc + i0 + 3);
+        cx<T> bcv[4];
+        ld_tw_row<T, 4>(cd.bc + i0, bcv);  // (b, c) of the four voxels, vector loads
+        const cx<T> bc0 = bcv[0], bc1 = bcv[1], bc2 = bcv[2], bc3 = bcv[3];
         Z0[q].re = bc0.im + bc0.re * Z0[q].re + sqrt(tau * bc0.re) * g0;
         Z0[q].im = bc1.im + bc1.re * Z0[q].im + sqrt(tau * bc1.re) * g1;
         Z1[q].re = bc2.im + bc2.re * Z1[q].re + sqrt(tau * bc2.re) * g2;
@@ -224,12 +269,13 @@ __global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const ChainDev<T>* __
     if constexpr (MODE != kModeMaterialize) {
       Dft<Q2, -1, T>::run(Z0);
       Dft<Q2, -1, T>::run(Z1);
+      cx<T> w0[Q2], w1[Q2];
+      ld_tw_row<T, Q2>(tw + TL::kRpv + pp * Q2, w0);
+      ld_tw_row<T, Q2>(tw + TL::kRpv + (pp + 1) * Q2, w1);
 #pragma unroll
       for (int v = 0; v < Q2; ++v) {
-        const cx<T> y0 = (pp * v == 0) ? Z0[v] : cmul(Z0[v], ldc<T>(tw + 2 * pp * v));
-        const cx<T> y1 = cmul(Z1[v], ldc<T>(tw + 2 * (pp + 1) * v));
-        stc<T>(row + pp * Q2 + v, y0);
-        stc<T>(row + (pp + 1) * Q2 + v, y1);
+        stc<T>(row + pp * Q2 + v, v == 0 ? Z0[v] : cmul(Z0[v], w0[v]));
+        stc<T>(row + (pp + 1) * Q2 + v, v == 0 ? Z1[v] : cmul(Z1[v], w1[v]));
       }
     }
   }
@@ -286,29 +332,50 @@ __global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const ChainDev<T>* __
 #pragma unroll
     for (int q = 0; q < Q; ++q) Z[q] = ldc<T>(rows + (pl * Q + q) * RS + l);
     Dft<Q, -1, T>::run(Z);
+    cx<T> w[Q];
+    ld_tw_row<T, Q>(tw + TL::kCpv + p * Q, w);
 #pragma unroll
-    for (int v = 0; v < Q; ++v) {
-      const cx<T> y = (p * v == 0) ? Z[v] : cmul(Z[v], ldc<T>(tw + p * v));
-      stc<T>(rows + (pl * Q + v) * RS + l, y);
-    }
+    for (int v = 0; v < Q; ++v) stc<T>(rows + (pl * Q + v) * RS + l, v == 0 ? Z[v] : cmul(Z[v], w[v]));
   }
   cluster_barrier<C>();
 
   // Column stage F2 (per v of this CTA): DFT_P over p of slot p*Q + v (any
   // CTA) -> X[Q u + v] -> global; the packed column 0 goes to CTA 0's scratch.
-  for (int it = threadIdx.x; it < H * QC; it += NT) {
-    const int l = it % H;
-    const int v = int(rank) * QC + it / H;
-    cx<T> X[P];
+  constexpr int TF2 = H * QC;
+  constexpr int BF = TF2 >= 2 * NT ? 2 : 1;
+  for (int it0 = threadIdx.x; it0 < TF2; it0 += BF * NT) {
+    cx<T> X[BF][P];
 #pragma unroll
-    for (int p = 0; p < P; ++p) X[p] = ldc<T>(rbase[p / PC] + ((p % PC) * Q + v) * RS + l);
-    Dft<P, -1, T>::run(X);
-    if (l != 0) {
+    for (int b = 0; b < BF; ++b) {
+      const int it = it0 + b * NT;
+      if (it < TF2) {
+        const int l = it % H;
+        const int v = int(rank) * QC + it / H;
 #pragma unroll
-      for (int u = 0; u < P; ++u) stc<T>(mainp + size_t(Q * u + v) * H + l, X[u]);
-    } else {
+        for (int p = 0; p < P; ++p) {
+          const int off = ((p % PC) * Q + v) * RS + l;
+          if constexpr (C == 1) X[b][p] = ldc<T>(rows + off);
+          else X[b][p] = ld_dsmem(rbase[p / PC] + uint32_t(off) * kEl, T(0));
+        }
+      }
+    }
 #pragma unroll
-      for (int u = 0; u < P; ++u) stc<T>(col0_r0 + Q * u + v, X[u]);
+    for (int b = 0; b < BF; ++b) {
+      const int it = it0 + b * NT;
+      if (it >= TF2) continue;
+      const int l = it % H;
+      const int v = int(rank) * QC + it / H;
+      Dft<P, -1, T>::run(X[b]);
+      if (l != 0) {
+#pragma unroll
+        for (int u = 0; u < P; ++u) stc<T>(mainp + size_t(Q * u + v) * H + l, X[b][u]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+          if constexpr (C == 1) stc<T>(col0 + Q * u + v, X[b][u]);
+          else st_dsmem(col0_r0 + uint32_t(Q * u + v) * kEl, X[b][u]);
+        }
+      }
     }
   }
   cluster_barrier<C>();

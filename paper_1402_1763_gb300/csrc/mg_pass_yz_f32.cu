@@ -4,11 +4,10 @@
 namespace mg {
 
 template <>
-cudaError_t launch_pass_yz<float>(int n, int C, int mode, const ChainDev<float>* d, int nc, const uint32_t* sw,
-                                  const void* tw, cudaStream_t st) {
+cudaError_t launch_pass_yz<float>(int n, int C, int mode, const LaunchArgs<float>& args, cudaStream_t st) {
   using namespace yzimpl;
 #define MG_CASE(N_, C_) \
-  if (n == N_ && C == C_) return run_mode<float, N_, C_>(mode, d, nc, sw, tw, st);
+  if (n == N_ && C == C_) return run_mode<float, N_, C_>(mode, args, st);
   MG_CASE(8, 1)
   MG_CASE(12, 1)
   MG_CASE(16, 1)

@@ -19,8 +19,8 @@ constexpr int yz_threads() {
 }
 
 template <typename T, int N, int C, int MODE>
-cudaError_t run(const ChainDev<T>* d_chains, int n_chains, const uint32_t* d_sweep, const void* tw,
-                cudaStream_t st) {
+cudaError_t run(const LaunchArgs<T>& args, cudaStream_t st) {
+  const int n_chains = args.n_chains;
   constexpr int NT = yz_threads<T, N, C>();
   using S = PassYZShape<T, N, C>;
   auto kern = pass_yz_kernel<T, N, C, MODE, NT, yz_minblocks<T, N, C>()>;
@@ -38,20 +38,18 @@ cudaError_t run(const ChainDev<T>* d_chains, int n_chains, const uint32_t* d_swe
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, d_chains, n_chains, d_sweep,
-                            static_cast<const typename VT<T>::c2*>(tw));
+  return cudaLaunchKernelEx(&cfg, kern, args);
 }
 
 template <typename T, int N, int C>
-cudaError_t run_mode(int mode, const ChainDev<T>* d_chains, int n_chains, const uint32_t* d_sweep,
-                     const void* tw, cudaStream_t st) {
+cudaError_t run_mode(int mode, const LaunchArgs<T>& args, cudaStream_t st) {
   switch (mode) {
     case kModeSweep:
-      return run<T, N, C, kModeSweep>(d_chains, n_chains, d_sweep, tw, st);
+      return run<T, N, C, kModeSweep>(args, st);
     case kModeMaterialize:
-      return run<T, N, C, kModeMaterialize>(d_chains, n_chains, d_sweep, tw, st);
+      return run<T, N, C, kModeMaterialize>(args, st);
     case kModeLoad:
-      return run<T, N, C, kModeLoad>(d_chains, n_chains, d_sweep, tw, st);
+      return run<T, N, C, kModeLoad>(args, st);
     default:
       return cudaErrorInvalidValue;
   }
