@@ -66,6 +66,19 @@ def algorithmic_bytes(n: int, chains: int, esz: int):
     return yz, x
 
 
+def kernel_source_hash() -> str:
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1402_1763_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))
+                   + glob.glob(os.path.join(csrc, "*.h")))
+    h = hashlib.sha256()
+    for fn in files:
+        with open(fn, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -223,11 +236,13 @@ def main():
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     sweep_bytes = yz_bytes + x_bytes
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    prof = os.path.join(ROOT, "profiles", "pass_traffic_256cubed_fp32_16chains.json")
     if os.path.exists(prof):
         with open(prof) as f:
             tr = json.load(f)
-        traffic = tr.get(dom)
+        # counters only count for the kernel build they were taken on
+        if tr.get("source_hash") == kernel_source_hash():
+            traffic = tr["per_launch_bytes"].get(dom)
 
     # end to end through the public API with host buffers: each step sweeps
     # all chains and reads every chain's P(k) back to pinned host memory
