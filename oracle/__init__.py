@@ -10,6 +10,7 @@ Modules:
   philox   Philox4x32-10 and Box-Muller normals (Sec. 3.4's per-core RNGs)
   bins     k-shell table, dof weights, conjugate partners (Sec. 3.2)
   sampler  tau and N~ (Sec. 2), Alg. 1, Alg. 2 on shells, the chain driver
+  adjoint  torch FP64 autograd of a fixed-P chain of sweeps (differentiation workload)
 
 Parity status of each function is listed in DESIGN.md ("oracle pins").
 """
