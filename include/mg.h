@@ -153,6 +153,25 @@ mg_status mg_set_s(mg_ctx* ctx, int32_t chain, const void* s, int32_t s_is_devic
 /* Replace one chain's P (n_bins+1 host doubles, all > 0). */
 mg_status mg_set_pk(mg_ctx* ctx, int32_t chain, const double* P);
 
+/* Replace the data d of one data set (group) — M host doubles, finite — keeping
+ * N and R: the messenger constants c = gamma d are recomputed, with
+ * gamma = tau R / (tau R^2 + N~) (Sec. 3.1, t-conditional).  Chains keep
+ * their state. */
+mg_status mg_set_data(mg_ctx* ctx, int32_t group, const double* d);
+
+/* Differentiation of K sweeps (K >= 1) of one chain with P = exp(logP) held
+ * fixed and the Philox noise of the chain's next K sweeps held fixed, from the
+ * chain's current state s_0.  Loss L = sum_j w_j |s_hat_K,j|^2 over the stored
+ * modes of the K-th sample, w in the stored-mode layout [kx][ky][kz] with
+ * kz in [0, n/2] (n*n*(n/2+1) host doubles).  Writes L to *loss, dL/dlogP to
+ * dlogP (n_bins+1 host doubles) and dL/dd to dd (M host doubles).  The
+ * gradients come from a hand-written adjoint of the sweep (transposed FFTs and
+ * transposed per-voxel / per-mode affine maps) with the state checkpointed
+ * after every forward sweep.  The chain's state, P and the sweep counter are
+ * restored before returning.  Synchronises. */
+mg_status mg_adjoint(mg_ctx* ctx, int32_t chain, int32_t K, const double* logP, const double* w, double* loss,
+                     double* dlogP, double* dd);
+
 /* Sweep counter (Philox counter word 1 of the next sweep); mg_set_sweep_count
  * restores it when resuming from a checkpoint. */
 mg_status mg_get_sweep_count(mg_ctx* ctx, int64_t* out);
@@ -164,7 +183,8 @@ mg_status mg_chain_info(mg_ctx* ctx, int32_t chain, int32_t* n, int32_t* n_bins,
 /* Wait for all enqueued work and report any sticky device status. */
 mg_status mg_sync(mg_ctx* ctx);
 
-/* Human-readable description of the last error on ctx (never NULL). */
+/* Human-readable description of the last error on ctx (never NULL); with
+ * ctx == NULL, why the calling thread's last mg_init / mg_init_batch failed. */
 const char* mg_last_error(const mg_ctx* ctx);
 
 /* Free everything the context owns; ctx may be NULL. */

@@ -71,6 +71,8 @@ def library():
         "mg_read_stats": (C.c_int, [_P, C.c_int32, C.POINTER(MgStats)]),
         "mg_set_s": (C.c_int, [_P, C.c_int32, _P, C.c_int32]),
         "mg_set_pk": (C.c_int, [_P, C.c_int32, _D]),
+        "mg_set_data": (C.c_int, [_P, C.c_int32, _D]),
+        "mg_adjoint": (C.c_int, [_P, C.c_int32, C.c_int32, _D, _D, _D, _D, _D]),
         "mg_get_sweep_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
         "mg_set_sweep_count": (C.c_int, [_P, C.c_int64]),
         "mg_chain_info": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -91,7 +93,7 @@ def library():
 
 def _check(status: int, ctx=None):
     if status != MG_OK:
-        msg = library().mg_last_error(ctx).decode() if ctx else ""
+        msg = library().mg_last_error(ctx).decode()
         raise MgError(status, msg or "call failed")
 
 
@@ -193,6 +195,25 @@ def mg_set_s(ctx, chain: int, ptr: int, is_device: bool):
 
 def mg_set_pk(ctx, chain: int, P: np.ndarray):
     _check(library().mg_set_pk(ctx, int(chain), _dptr(P)), ctx)
+
+
+def mg_set_data(ctx, group: int, d):
+    _check(library().mg_set_data(ctx, int(group), _dptr(_f64(d))), ctx)
+
+
+def mg_adjoint(ctx, chain: int, K: int, logP, w):
+    """(L, dL/dlogP, dL/dd) of K fixed-P sweeps; see include/mg.h."""
+    lp = _f64(logP)
+    wa = _f64(w)
+    n = mg_chain_info(ctx, chain)[0]
+    if wa.size != n * n * (n // 2 + 1):
+        raise ValueError("w must hold n*n*(n/2+1) stored-mode weights")
+    L = np.zeros(1)
+    gl = np.empty(lp.size)
+    gd = np.empty(n ** 3)
+    _check(library().mg_adjoint(ctx, int(chain), int(K), _dptr(lp), _dptr(wa), _dptr(L), _dptr(gl),
+                                _dptr(gd)), ctx)
+    return float(L[0]), gl, gd.reshape(n, n, n)
 
 
 def mg_get_sweep_count(ctx) -> int:
@@ -336,6 +357,12 @@ class Sampler:
 
     def set_pk(self, chain, P):
         mg_set_pk(self.ctx, chain, _f64(P))
+
+    def set_data(self, group, d):
+        mg_set_data(self.ctx, group, d)
+
+    def adjoint(self, chain, K, logP, w):
+        return mg_adjoint(self.ctx, chain, K, logP, w)
 
     @property
     def sweep_count(self) -> int:

@@ -38,7 +38,7 @@ struct Group {
   double tau = 0;
   size_t M = 0;
   std::vector<long long> n_b;  // B+1
-  std::shared_ptr<DevBuf> bc, bin_of_m2, n_b_dev;
+  std::shared_ptr<DevBuf> bc, bin_of_m2, n_b_dev, gamma;
 };
 
 struct Chain {
@@ -82,7 +82,10 @@ struct mg_ctx {
 
 namespace {
 
+thread_local std::string g_create_error;  // why the last mg_init / mg_init_batch failed
+
 mg_status fail(mg_ctx* c, mg_status s, const std::string& msg) {
+  g_create_error = msg;
   if (c) {
     c->err = msg;
     if (s == MG_ECUDA || s == MG_ENUMERIC || s == MG_ETIMEOUT) c->sticky = s;
@@ -301,7 +304,7 @@ mg_status enqueue_passes(mg_ctx* c, int which) {
   if (which & 2) {
     for (auto& sc : c->classes)
       for (auto& blob : sc.args)
-        MG_CUDA(c, launch_pass_x<T>(sc.n, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()), sc.B_max, c->stream));
+        MG_CUDA(c, launch_pass_x<T>(sc.n, 0, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()), sc.B_max, c->stream));
   }
   if (which & 4) return launch_shell_draw<T>(c, 1, true);
   return MG_OK;
@@ -364,6 +367,177 @@ mg_status load_s(mg_ctx* c, int chain, const T* in_dev) {
   if (s != MG_OK) return s;
   MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, 2, a, c->stream));
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Differentiation: K fixed-P sweeps from the chain's current state with the
+// noise of its next K sweeps, the loss L = sum_j w_j |s_hat_K,j|^2, and the
+// adjoint sweeps back to the start (per-sweep checkpoints of the state).  The
+// chain's state, P and sweep counter are restored afterwards.
+// ---------------------------------------------------------------------------
+
+template <typename T>
+mg_status upload_desc(mg_ctx* c, const ChainDev<T>& h, std::shared_ptr<DevBuf>* buf, LaunchArgs<T>* a) {
+  cudaError_t e;
+  *buf = dalloc(sizeof(h), &e);
+  MG_CUDA(c, e);
+  MG_CUDA(c, cudaMemcpyAsync((*buf)->p, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  a->chains = static_cast<const ChainDev<T>*>((*buf)->p);
+  return MG_OK;
+}
+
+template <typename T>
+mg_status set_sweep_ctr(mg_ctx* c, uint32_t v) {
+  MG_CUDA(c, cudaMemcpyAsync(c->d_sweep->p, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+template <typename T>
+mg_status adjoint_impl(mg_ctx* c, int chain, int K, const double* logP, const double* wl_host, double* loss_out,
+                       double* dlogP, double* dd_out) {
+  using V2 = typename VT<T>::c2;
+  Chain& ch = c->chains[chain];
+  const Group& g = c->groups[ch.group];
+  const int n = g.n, H = n / 2, B1 = g.B + 1;
+  const size_t Mh = size_t(n) * n * (H + 1);
+  const size_t main_b = size_t(n) * n * H * sizeof(V2), nyq_b = size_t(n) * n * sizeof(V2);
+  const size_t state_b = main_b + nyq_b;
+  SizeClass* sc;
+  std::shared_ptr<DevBuf> d0;
+  LaunchArgs<T> base;
+  mg_status st = single_chain_args<T>(c, chain, nullptr, nullptr, &sc, &d0, &base);
+  if (st != MG_OK) return st;
+  ChainDev<T> cd0;
+  MG_CUDA(c, cudaMemcpy(&cd0, base.chains, sizeof(cd0), cudaMemcpyDeviceToHost));
+  cudaError_t e;
+  auto ck = dalloc(state_b * size_t(K + 1), &e);
+  MG_CUDA(c, e);
+  auto scr = dalloc(state_b, &e);
+  MG_CUDA(c, e);
+  auto adj = dalloc(state_b, &e);
+  MG_CUDA(c, e);
+  auto wl = dalloc(Mh * sizeof(T), &e);
+  MG_CUDA(c, e);
+  auto dd = dalloc(g.M * sizeof(T), &e);
+  MG_CUDA(c, e);
+  auto acc = dalloc(size_t(2) * B1 * sizeof(double), &e);
+  MG_CUDA(c, e);
+  auto Psave = dalloc(size_t(B1) * sizeof(double), &e);
+  MG_CUDA(c, e);
+  auto ddw = dalloc(g.M * sizeof(double), &e);
+  MG_CUDA(c, e);
+  {
+    LaunchArgs<T> none;  // set the adjoint kernels' attributes (outside any capture)
+    std::memset(&none, 0, sizeof(none));
+    MG_CUDA(c, launch_pass_yz<T>(n, sc->C, 3, none, c->stream));
+    MG_CUDA(c, launch_pass_x<T>(n, 1, none, sc->B_max, c->stream));
+    MG_CUDA(c, launch_pass_x<T>(n, 2, none, sc->B_max, c->stream));
+  }
+  char* ckp = static_cast<char*>(ck->p);
+  auto ck_main = [&](int k) { return reinterpret_cast<V2*>(ckp + size_t(k) * state_b); };
+  auto ck_nyq = [&](int k) { return reinterpret_cast<V2*>(ckp + size_t(k) * state_b + main_b); };
+  V2* scr_main = static_cast<V2*>(scr->p);
+  V2* scr_nyq = reinterpret_cast<V2*>(static_cast<char*>(scr->p) + main_b);
+  V2* adj_main = static_cast<V2*>(adj->p);
+  V2* adj_nyq = reinterpret_cast<V2*>(static_cast<char*>(adj->p) + main_b);
+  cudaStream_t s = c->stream;
+
+  // save the chain and set P = exp(logP)
+  uint32_t sw0 = 0;
+  MG_CUDA(c, cudaMemcpyAsync(&sw0, c->d_sweep->p, sizeof(sw0), cudaMemcpyDeviceToHost, s));
+  MG_CUDA(c, cudaMemcpyAsync(Psave->p, ch.P->p, size_t(B1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  MG_CUDA(c, cudaMemcpyAsync(ck_main(0), ch.main->p, main_b, cudaMemcpyDeviceToDevice, s));
+  MG_CUDA(c, cudaMemcpyAsync(ck_nyq(0), ch.nyq->p, nyq_b, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> Pn(B1);
+  for (int b = 0; b < B1; ++b) Pn[b] = std::exp(logP[b]);
+  MG_CUDA(c, cudaMemcpyAsync(ch.P->p, Pn.data(), size_t(B1) * sizeof(double), cudaMemcpyHostToDevice, s));
+  st = launch_shell_draw<T>(c, 0, false);
+  if (st != MG_OK) return st;
+  // On the kz = 0 and n/2 planes both k and -k are stored; the loss counts
+  // each with its own weight, but the transforms act on the Hermitian part of a
+  // plane only, so the adjoint seed must use the pair's mean weight (the loss
+  // is the same since |s_hat(k)| = |s_hat(-k)|).
+  std::vector<T> wlt(Mh);
+  for (int kx = 0; kx < n; ++kx)
+    for (int ky = 0; ky < n; ++ky)
+      for (int kz = 0; kz <= H; ++kz) {
+        const size_t j = (size_t(kx) * n + ky) * (H + 1) + kz;
+        double wv = wl_host[j];
+        if (kz == 0 || kz == H) {
+          const size_t jp = (size_t((n - kx) % n) * n + (n - ky) % n) * (H + 1) + kz;
+          wv = 0.5 * (wl_host[j] + wl_host[jp]);
+        }
+        wlt[j] = T(wv);
+      }
+  MG_CUDA(c, cudaMemcpyAsync(wl->p, wlt.data(), Mh * sizeof(T), cudaMemcpyHostToDevice, s));
+  MG_CUDA(c, cudaMemsetAsync(dd->p, 0, g.M * sizeof(T), s));
+  MG_CUDA(c, cudaMemsetAsync(acc->p, 0, size_t(2) * B1 * sizeof(double), s));
+
+  // forward: K sweeps of this chain with P fixed, checkpointing every state
+  for (int k = 1; k <= K; ++k) {
+    if ((st = set_sweep_ctr<T>(c, sw0 + uint32_t(k - 1))) != MG_OK) return st;
+    MG_CUDA(c, launch_pass_yz<T>(n, sc->C, 0, base, s));
+    MG_CUDA(c, launch_pass_x<T>(n, 0, base, sc->B_max, s));
+    MG_CUDA(c, cudaMemcpyAsync(ck_main(k), ch.main->p, main_b, cudaMemcpyDeviceToDevice, s));
+    MG_CUDA(c, cudaMemcpyAsync(ck_nyq(k), ch.nyq->p, nyq_b, cudaMemcpyDeviceToDevice, s));
+  }
+
+  // adjoint sweeps K .. 1
+  ChainDev<T> cs = cd0, cx = cd0, cy = cd0;
+  cs.main = scr_main;
+  cs.nyq = scr_nyq;
+  cx.main = adj_main;
+  cx.nyq = adj_nyq;
+  cx.main2 = scr_main;
+  cx.nyq2 = scr_nyq;
+  cx.wloss = static_cast<const T*>(wl->p);
+  cy.main = adj_main;
+  cy.nyq = adj_nyq;
+  cy.gamma = static_cast<const T*>(g.gamma->p);
+  cy.dd = static_cast<T*>(dd->p);
+  std::shared_ptr<DevBuf> bs, bx_top, bx_mid, by;
+  LaunchArgs<T> as = base, ax_top = base, ax_mid = base, ay = base;
+  if ((st = upload_desc<T>(c, cs, &bs, &as)) != MG_OK) return st;
+  if ((st = upload_desc<T>(c, cy, &by, &ay)) != MG_OK) return st;
+  cx.main_in = ck_main(K);  // the last sweep starts from the final state
+  cx.nyq_in = ck_nyq(K);
+  if ((st = upload_desc<T>(c, cx, &bx_top, &ax_top)) != MG_OK) return st;
+  cx.main_in = adj_main;  // earlier sweeps transform the adjoint state in place
+  cx.nyq_in = adj_nyq;
+  if ((st = upload_desc<T>(c, cx, &bx_mid, &ax_mid)) != MG_OK) return st;
+  double* grad = static_cast<double*>(acc->p);
+  for (int k = K; k >= 1; --k) {
+    if ((st = set_sweep_ctr<T>(c, sw0 + uint32_t(k - 1))) != MG_OK) return st;
+    // recompute the forward messenger field of sweep k: y/z transform of t_k
+    MG_CUDA(c, cudaMemcpyAsync(scr_main, ck_main(k - 1), main_b, cudaMemcpyDeviceToDevice, s));
+    MG_CUDA(c, cudaMemcpyAsync(scr_nyq, ck_nyq(k - 1), nyq_b, cudaMemcpyDeviceToDevice, s));
+    MG_CUDA(c, launch_pass_yz<T>(n, sc->C, 0, as, s));
+    MG_CUDA(c, launch_pass_x<T>(n, k == K ? 1 : 2, k == K ? ax_top : ax_mid, sc->B_max, s));
+    adjoint_reduce_kernel<<<B1, 256, 0, s>>>(cd0.partial, pass_x_tiles(n), B1, grad, grad + B1);
+    MG_CUDA(c, cudaGetLastError());
+    MG_CUDA(c, launch_pass_yz<T>(n, sc->C, 3, ay, s));
+  }
+  widen_kernel<T><<<1024, 256, 0, s>>>(static_cast<const T*>(dd->p), g.M, static_cast<double*>(ddw->p));
+  MG_CUDA(c, cudaGetLastError());
+  std::vector<double> hb(size_t(2) * B1);
+  MG_CUDA(c, cudaMemcpyAsync(hb.data(), grad, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MG_CUDA(c, cudaMemcpyAsync(dd_out, ddw->p, g.M * sizeof(double), cudaMemcpyDeviceToHost, s));
+  // restore the chain
+  MG_CUDA(c, cudaMemcpyAsync(ch.main->p, ck_main(0), main_b, cudaMemcpyDeviceToDevice, s));
+  MG_CUDA(c, cudaMemcpyAsync(ch.nyq->p, ck_nyq(0), nyq_b, cudaMemcpyDeviceToDevice, s));
+  MG_CUDA(c, cudaMemcpyAsync(ch.P->p, Psave->p, size_t(B1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  st = launch_shell_draw<T>(c, 0, false);
+  if (st != MG_OK) return st;
+  if ((st = set_sweep_ctr<T>(c, sw0)) != MG_OK) return st;
+  double L = 0.0;
+  for (int b = 0; b < B1; ++b) {
+    dlogP[b] = hb[b];
+    L += hb[B1 + b];
+  }
+  *loss_out = L;
   return MG_OK;
 }
 
@@ -472,9 +646,11 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
     MG_CUDA(c, cudaMemsetAsync(c->d_status->p, 0, sizeof(int), c->stream));
     g.bc = dalloc(g.M * sizeof(V2), &e);
     MG_CUDA(c, e);
+    g.gamma = dalloc(g.M * sizeof(T), &e);
+    MG_CUDA(c, e);
     messenger_constants_kernel<T><<<1024, 256, 0, c->stream>>>(
         static_cast<const double*>(dN->p), static_cast<const double*>(dR->p), static_cast<const double*>(dd->p), g.M,
-        g.tau, static_cast<V2*>(g.bc->p));
+        g.tau, static_cast<V2*>(g.bc->p), static_cast<T*>(g.gamma->p));
     MG_CUDA(c, cudaGetLastError());
     // shells
     const auto tab = build_bin_table(g.n, g.L, g.B, edges, &g.n_b);
@@ -556,7 +732,7 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
     LaunchArgs<T> none;
     std::memset(&none, 0, sizeof(none));  // n_chains = 0: set kernel attributes only
     for (int mode = 0; mode < 3; ++mode) MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, mode, none, c->stream));
-    MG_CUDA(c, launch_pass_x<T>(sc.n, none, sc.B_max, c->stream));
+    MG_CUDA(c, launch_pass_x<T>(sc.n, 0, none, sc.B_max, c->stream));
   }
   s = launch_shell_draw<T>(c, 0, false);
   if (s != MG_OK) return s;
@@ -569,27 +745,28 @@ mg_status create(mg_ctx** out, int32_t n_groups, const mg_grid* grids, const dou
                  const int32_t* n_bins, const uint64_t* seeds, const mg_options* opt_in) {
   if (!out) return MG_EINVAL;
   *out = nullptr;
-  if (n_groups < 1 || !grids || !N || !R || !d || !n_bins || !seeds) return MG_EINVAL;
+  if (n_groups < 1 || !grids || !N || !R || !d || !n_bins || !seeds)
+    return fail(nullptr, MG_EINVAL, "null argument or n_groups < 1");
   mg_options opt;
   mg_options_init(&opt);
   if (opt_in) opt = *opt_in;
-  if (opt.precision != 32 && opt.precision != 64) return MG_EINVAL;
-  if (opt.n_chains < 1 || opt.chain_id0 < 0) return MG_EINVAL;
-  if (!(opt.tau_scale > 0.0 && opt.tau_scale <= 1.0)) return MG_EINVAL;
-  if (opt.record_every < 0) return MG_EINVAL;
-  if (opt.yz_cluster < 0) return MG_EINVAL;
+  if (opt.precision != 32 && opt.precision != 64) return fail(nullptr, MG_EINVAL, "precision must be 32 or 64");
+  if (opt.n_chains < 1 || opt.chain_id0 < 0) return fail(nullptr, MG_EINVAL, "n_chains >= 1, chain_id0 >= 0");
+  if (!(opt.tau_scale > 0.0 && opt.tau_scale <= 1.0)) return fail(nullptr, MG_EINVAL, "tau_scale in (0, 1]");
+  if (opt.record_every < 0) return fail(nullptr, MG_EINVAL, "record_every >= 0");
+  if (opt.yz_cluster < 0) return fail(nullptr, MG_EINVAL, "yz_cluster >= 0");
   for (int g = 0; g < n_groups; ++g) {
     mg_status s = validate_grid(&grids[g]);
-    if (s != MG_OK) return s;
-    if (n_bins[g] < 1 || n_bins[g] > kMaxBins) return MG_EINVAL;
-    if (!N[g] || !R[g] || !d[g]) return MG_EINVAL;
+    if (s != MG_OK) return fail(nullptr, s, "grid must be cubic with equal sides and n in {8,12,16,24,32,48,64,96,128,192,256}");
+    if (n_bins[g] < 1 || n_bins[g] > kMaxBins) return fail(nullptr, MG_EINVAL, "1 <= n_bins <= 254");
+    if (!N[g] || !R[g] || !d[g]) return fail(nullptr, MG_EINVAL, "null data array");
     if (opt.P0)
       for (int b = 0; b <= n_bins[g]; ++b)
-        if (!(opt.P0[b] > 0.0) || !std::isfinite(opt.P0[b])) return MG_EINVAL;
+        if (!(opt.P0[b] > 0.0) || !std::isfinite(opt.P0[b])) return fail(nullptr, MG_EINVAL, "P0 must be positive and finite");
   }
   if (opt.P0) {
     for (int g = 1; g < n_groups; ++g)
-      if (n_bins[g] != n_bins[0]) return MG_EINVAL;  // one P0 shared by all groups
+      if (n_bins[g] != n_bins[0]) return fail(nullptr, MG_EINVAL, "P0 needs equal n_bins in all groups");
   }
   auto* c = new mg_ctx();
   c->precision = opt.precision;
@@ -847,6 +1024,49 @@ mg_status mg_set_pk(mg_ctx* c, int32_t chain, const double* P) {
   return check_status(c);
 }
 
+mg_status mg_set_data(mg_ctx* c, int32_t group, const double* d) {
+  if (!c || !d) return MG_EINVAL;
+  if (c->sticky != MG_OK) return c->sticky;
+  if (group < 0 || size_t(group) >= c->groups.size()) return fail(c, MG_EINVAL, "group index out of range");
+  const Group& g = c->groups[group];
+  for (size_t i = 0; i < g.M; ++i)
+    if (!std::isfinite(d[i])) return fail(c, MG_EINVAL, "d must be finite");
+  cudaError_t e;
+  auto dd = dalloc(g.M * sizeof(double), &e);
+  MG_CUDA(c, e);
+  MG_CUDA(c, cudaMemcpyAsync(dd->p, d, g.M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (c->precision == 32)
+    set_data_kernel<float><<<1024, 256, 0, c->stream>>>(static_cast<const float*>(g.gamma->p),
+                                                        static_cast<const double*>(dd->p), g.M,
+                                                        static_cast<float2*>(g.bc->p));
+  else
+    set_data_kernel<double><<<1024, 256, 0, c->stream>>>(static_cast<const double*>(g.gamma->p),
+                                                         static_cast<const double*>(dd->p), g.M,
+                                                         static_cast<double2*>(g.bc->p));
+  MG_CUDA(c, cudaGetLastError());
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
+mg_status mg_adjoint(mg_ctx* c, int32_t chain, int32_t K, const double* logP, const double* w, double* loss,
+                     double* dlogP, double* dd) {
+  if (!c || !logP || !w || !loss || !dlogP || !dd) return MG_EINVAL;
+  if (c->sticky != MG_OK) return c->sticky;
+  if (!valid_chain(c, chain)) return fail(c, MG_EINVAL, "chain index out of range");
+  if (K < 1) return fail(c, MG_EINVAL, "K must be >= 1");
+  const Group& g = c->groups[c->chains[chain].group];
+  // the adjoint x pass holds two pencil tiles in shared memory
+  if (c->precision == 64 && g.n > 192)
+    return fail(c, MG_EUNSUPPORTED, "the FP64 adjoint is built for n <= 192");
+  for (int b = 0; b <= g.B; ++b)
+    if (!std::isfinite(logP[b])) return fail(c, MG_EINVAL, "logP must be finite");
+  const mg_status s = c->precision == 32 ? adjoint_impl<float>(c, chain, K, logP, w, loss, dlogP, dd)
+                                         : adjoint_impl<double>(c, chain, K, logP, w, loss, dlogP, dd);
+  if (s != MG_OK) return s;
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
 mg_status mg_get_sweep_count(mg_ctx* c, int64_t* out) {
   if (!c || !out) return MG_EINVAL;
   uint32_t v = 0;
@@ -885,7 +1105,7 @@ mg_status mg_sync(mg_ctx* c) {
 }
 
 const char* mg_last_error(const mg_ctx* c) {
-  if (!c) return "null context";
+  if (!c) return g_create_error.empty() ? "null context" : g_create_error.c_str();
   return c->err.c_str();
 }
 

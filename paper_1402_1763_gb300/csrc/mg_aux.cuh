@@ -51,25 +51,71 @@ __global__ void tau_bound_kernel(const double* __restrict__ N, const double* __r
 //               c = tau / (tau R^2 + N~) * R * d
 //   unobserved: b = 1, c = 0   (mu = s, sigma^2 = T).
 // Products and sums are rounded one by one (no FMA contraction).
+// Also writes gamma = dc/dd = tau R / (tau R^2 + N~) (0 unobserved), the
+// factor through which the data enter the messenger draw.
 template <typename T>
 __global__ void messenger_constants_kernel(const double* __restrict__ N, const double* __restrict__ R,
                                            const double* __restrict__ d, size_t M, double tau,
-                                           typename VT<T>::c2* __restrict__ bc) {
+                                           typename VT<T>::c2* __restrict__ bc, T* __restrict__ gamma) {
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < M; i += size_t(gridDim.x) * blockDim.x) {
     const double r = R[i];
-    double b = 1.0, c = 0.0;
+    double b = 1.0, c = 0.0, gm = 0.0;
     if (__dmul_rn(r, r) > 0.0) {
       double nt = __dsub_rn(N[i], __dmul_rn(__dmul_rn(r, tau), r));
       nt = nt > 0.0 ? nt : 0.0;
       const double den = __dadd_rn(__dmul_rn(tau, __dmul_rn(r, r)), nt);
       b = __ddiv_rn(nt, den);
-      c = __dmul_rn(__dmul_rn(__ddiv_rn(tau, den), r), d[i]);
+      gm = __dmul_rn(__ddiv_rn(tau, den), r);
+      c = __dmul_rn(gm, d[i]);
     }
     typename VT<T>::c2 v;
     v.x = T(b);
     v.y = T(c);
     bc[i] = v;
+    gamma[i] = T(gm);
   }
+}
+
+// New data d: c = gamma d (b does not depend on d).
+template <typename T>
+__global__ void set_data_kernel(const T* __restrict__ gamma, const double* __restrict__ d, size_t M,
+                                typename VT<T>::c2* __restrict__ bc) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < M; i += size_t(gridDim.x) * blockDim.x)
+    bc[i].y = T(double(gamma[i]) * d[i]);
+}
+
+// Adjoint: add one sweep's per-tile (gradient, loss) partials of every shell
+// to the running totals, summing the tiles in a fixed order.  Grid: B+1.
+__global__ void adjoint_reduce_kernel(const double* __restrict__ partial, int n_tiles, int B1,
+                                      double* __restrict__ grad, double* __restrict__ loss) {
+  const int b = blockIdx.x;
+  __shared__ double r1[256], r2[256];
+  double s1 = 0.0, s2 = 0.0;
+  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+    s1 += partial[(size_t(t) * B1 + b) * 2 + 0];
+    s2 += partial[(size_t(t) * B1 + b) * 2 + 1];
+  }
+  r1[threadIdx.x] = s1;
+  r2[threadIdx.x] = s2;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      r1[threadIdx.x] += r1[threadIdx.x + w];
+      r2[threadIdx.x] += r2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    grad[b] += r1[0];
+    loss[b] += r2[0];
+  }
+}
+
+// Widen the device-precision dL/dd to FP64 for the caller.
+template <typename T>
+__global__ void widen_kernel(const T* __restrict__ x, size_t M, double* __restrict__ y) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < M; i += size_t(gridDim.x) * blockDim.x)
+    y[i] = double(x[i]);
 }
 
 // Shell draw and the next sweep's per-shell coefficients.  One CTA per

@@ -52,6 +52,14 @@ struct ChainDev {
   const uint8_t* bin_of_m2;
   T* s_out;                        // real-space output of the materialise pass
   const T* s_in;                   // real-space input of the load pass
+  // adjoint passes only (see mg_adjoint):
+  const typename VT<T>::c2* main_in;  // pass X: first input state (else main)
+  const typename VT<T>::c2* nyq_in;
+  const typename VT<T>::c2* main2;    // pass X: the recomputed y/z transform of t
+  const typename VT<T>::c2* nyq2;
+  const T* wloss;                     // [n][n][n/2+1] loss weight per stored mode
+  const T* gamma;                     // [M] dc/dd = tau R / (tau R^2 + N~), 0 unobserved
+  T* dd;                              // [M] dL/dd accumulator
   T tau;
   int B;
 };

@@ -21,7 +21,8 @@ template <typename T>
 cudaError_t launch_pass_yz(int n, int C, int mode, const LaunchArgs<T>& args, cudaStream_t st);
 
 int pass_x_tiles(int n);
+// mode: 0 = sweep, 1 = adjoint of the last sweep, 2 = adjoint of an earlier sweep
 template <typename T>
-cudaError_t launch_pass_x(int n, const LaunchArgs<T>& args, int B_max, cudaStream_t st);
+cudaError_t launch_pass_x(int n, int mode, const LaunchArgs<T>& args, int B_max, cudaStream_t st);
 
 }  // namespace mg

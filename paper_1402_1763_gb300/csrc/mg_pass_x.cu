@@ -17,13 +17,13 @@ constexpr int pass_x_minblocks() {
   return (sizeof(T) == 4 && N >= 128) ? 3 : 1;
 }
 
-template <typename T, int N>
+template <typename T, int N, int MODE>
 cudaError_t run_x(const LaunchArgs<T>& args, int B_max, cudaStream_t st) {
   const int n_chains = args.n_chains;
   constexpr int NT = pass_x_threads<N>();
   using S = PassXShape<T, N>;
-  const size_t smem = S::smem_bytes(NT / 32, B_max);
-  auto kern = pass_x_kernel<T, N, NT, pass_x_minblocks<T, N>()>;
+  const size_t smem = S::smem_bytes(NT / 32, B_max, MODE != kXSweep);
+  auto kern = pass_x_kernel<T, N, NT, MODE == kXSweep ? pass_x_minblocks<T, N>() : 1, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess || n_chains == 0) return e;  // n_chains == 0: set attributes only
   const unsigned grid = unsigned(S::kTiles) * unsigned(n_chains);
@@ -37,12 +37,26 @@ int pass_x_tiles(int n) {
   return (n * (n / 2) + lw - 1) / lw + (n + lw - 1) / lw;
 }
 
+template <typename T, int N>
+cudaError_t run_x_mode(int mode, const LaunchArgs<T>& args, int B_max, cudaStream_t st) {
+  switch (mode) {
+    case kXSweep:
+      return run_x<T, N, kXSweep>(args, B_max, st);
+    case kXAdjTop:
+      return run_x<T, N, kXAdjTop>(args, B_max, st);
+    case kXAdjMid:
+      return run_x<T, N, kXAdjMid>(args, B_max, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
-cudaError_t launch_pass_x(int n, const LaunchArgs<T>& args, int B_max, cudaStream_t st) {
+cudaError_t launch_pass_x(int n, int mode, const LaunchArgs<T>& args, int B_max, cudaStream_t st) {
   switch (n) {
 #define MG_CASE(N_) \
   case N_:          \
-    return run_x<T, N_>(args, B_max, st);
+    return run_x_mode<T, N_>(mode, args, B_max, st);
     MG_CASE(8)
     MG_CASE(12)
     MG_CASE(16)
@@ -60,7 +74,7 @@ cudaError_t launch_pass_x(int n, const LaunchArgs<T>& args, int B_max, cudaStrea
   }
 }
 
-template cudaError_t launch_pass_x<float>(int, const LaunchArgs<float>&, int, cudaStream_t);
-template cudaError_t launch_pass_x<double>(int, const LaunchArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_pass_x<float>(int, int, const LaunchArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_pass_x<double>(int, int, const LaunchArgs<double>&, int, cudaStream_t);
 
 }  // namespace mg

@@ -145,6 +145,89 @@ __device__ __forceinline__ cx<T> draw_mode(cx<T> F, int kx, int ky, int kz, bool
   return s;
 }
 
+// The complex unit noise xi of one stored mode (the same draw draw_mode
+// makes), for the adjoint passes, which regenerate the forward noise.
+template <typename T, int N>
+__device__ __forceinline__ cx<T> mode_xi(int kx, int ky, int kz, uint32_t sweep, uint32_t k0, uint32_t k1,
+                                         uint32_t cid) {
+  constexpr int H = N / 2;
+  const uint32_t j = uint32_t((kx * N + ky) * (H + 1) + kz);
+  const T rs2 = T(0.70710678118654752440);
+  uint32_t src = j;
+  T sgn = T(1);
+  if (kz == 0 || kz == H) {
+    const uint32_t jp = uint32_t(((((N - kx) % N) * N) + ((N - ky) % N)) * (H + 1) + kz);
+    if (jp == j) {
+      const u32x4 w = philox4x32_10(j, sweep, cid, kStreamModes, k0, k1);
+      T z0, z1;
+      normal_pair<T>(w.x, w.y, z0, z1);
+      return {z0, T(0)};
+    }
+    if (jp < j) {
+      src = jp;
+      sgn = T(-1);
+    }
+  }
+  const u32x4 w = philox4x32_10(src, sweep, cid, kStreamModes, k0, k1);
+  T z0, z1;
+  normal_pair<T>(w.x, w.y, z0, z1);
+  return {z0 * rs2, sgn * (z1 * rs2)};
+}
+
+template <typename T, int N, int MODE>
+__device__ __forceinline__ cx<T> adjoint_mode(cx<T> G, cx<T> Ft, int kx, int ky, int kz, bool valid,
+                                              const ChainDev<T>& cd, uint32_t sweep, uint32_t k0, uint32_t k1,
+                                              uint32_t cid, int& bin, T& grad, T& loss);
+
+enum PassXMode : int {
+  kXSweep = 0,   // forward x FFT, signal draw, shell sums, inverse x FFT
+  kXAdjTop = 1,  // adjoint of the last sweep: loss from the final state, gradient terms
+  kXAdjMid = 2,  // adjoint of an earlier sweep
+};
+
+// Adjoint of the signal draw of one mode (fixed P).  In mode kXAdjTop, G is
+// the unnormalised x transform of the final state, i.e. n s_hat / sqrt(M); the
+// loss term is w_l |s_hat|^2 and the adjoint seed G = sqrt(M) mu with
+// mu = 2 w_l s_hat / w.  In kXAdjMid, G = sqrt(M) mu comes from the adjoint y/z
+// pass.  Ft is the unnormalised transform of the forward messenger field t.
+// With the shell's (a/M, sd/sqrt(M)) the gradient of log P_b gets
+// w (1 - a) Re(conj G (a/M Ft + sd/(2 sqrt M) xi)), and the value returned,
+// (a/M) G = a mu / sqrt(M), feeds the inverse transforms.
+template <typename T, int N, int MODE>
+__device__ __forceinline__ cx<T> adjoint_mode(cx<T> G, cx<T> Ft, int kx, int ky, int kz, bool valid,
+                                              const ChainDev<T>& cd, uint32_t sweep, uint32_t k0, uint32_t k1,
+                                              uint32_t cid, int& bin, T& grad, T& loss) {
+  constexpr int H = N / 2;
+  const int mx = kx <= H ? kx : kx - N;
+  const int my = ky <= H ? ky : ky - N;
+  const int m2 = mx * mx + my * my + kz * kz;
+  const bool edge = (kz == 0) || (kz == H);
+  const T wd = edge ? T(1) : T(2);
+  const bool dc = (m2 == 0);
+  bin = dc ? -1 : int(__ldg(cd.bin_of_m2 + m2));
+  const cx<T> cf = ldc<T>(cd.coef + (dc ? cd.B + 1 : bin));
+  loss = T(0);
+  if constexpr (MODE == kXAdjTop) {
+    const size_t j = size_t(kx * N + ky) * (H + 1) + kz;
+    const T wl = valid ? cd.wloss[j] : T(0);
+    const T M = T(double(N) * double(N) * double(N));
+    loss = wl * (M / (T(N) * T(N))) * (G.re * G.re + G.im * G.im);
+    const T sc = T(2) * wl * (M / T(N)) / wd;
+    G = {G.re * sc, G.im * sc};
+  }
+  const cx<T> xi = mode_xi<T, N>(kx, ky, kz, sweep, k0, k1, cid);
+  const T am = cf.re;  // a / M
+  const T a_ = am * T(double(N) * double(N) * double(N));
+  const cx<T> u = {am * Ft.re + T(0.5) * cf.im * xi.re, am * Ft.im + T(0.5) * cf.im * xi.im};
+  grad = wd * (T(1) - a_) * (G.re * u.re + G.im * u.im);
+  if (!valid || dc) {
+    bin = -1;
+    grad = T(0);
+    loss = T(0);
+  }
+  return {am * G.re, am * G.im};
+}
+
 template <typename T, int N>
 struct PassXShape {
   static constexpr int H = N / 2;
@@ -154,22 +237,24 @@ struct PassXShape {
   static constexpr int kNyqTiles = (N + LW - 1) / LW;
   static constexpr int kTiles = kMainTiles + kNyqTiles;
   static constexpr size_t kXchgBytes = size_t(N) * LW * sizeof(typename VT<T>::c2);
-  static size_t smem_bytes(int nwarps, int B) {
-    return kXchgBytes + size_t(nwarps) * (B + 1) * Acc<T>::kWords * sizeof(T);
+  static size_t smem_bytes(int nwarps, int B, bool dual = false) {
+    return (dual ? 2 : 1) * kXchgBytes + size_t(nwarps) * (B + 1) * Acc<T>::kWords * sizeof(T);
   }
 };
 
-template <typename T, int N, int NT, int MINB>
+template <typename T, int N, int NT, int MINB, int MODE = kXSweep>
 __global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const __grid_constant__ LaunchArgs<T> a) {
   using S = PassXShape<T, N>;
   using V2 = typename VT<T>::c2;
   using TL = TwLayout<N>;
   constexpr int H = S::H, P = S::P, Q = S::Q, LW = S::LW;
   constexpr int NW = NT / 32;
+  constexpr bool kAdj = MODE != kXSweep;
   static_assert(NT % 32 == 0, "whole warps");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V2* xs = reinterpret_cast<V2*>(smem_raw);  // [N][LW], slot p*Q + v
-  T* acc = reinterpret_cast<T*>(smem_raw + S::kXchgBytes);
+  V2* xs2 = reinterpret_cast<V2*>(smem_raw + S::kXchgBytes);  // adjoint: second input
+  T* acc = reinterpret_cast<T*>(smem_raw + (kAdj ? 2 : 1) * S::kXchgBytes);
 
   const int tile = blockIdx.x % S::kTiles;
   const int chain = blockIdx.x / S::kTiles;
@@ -184,35 +269,47 @@ __global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const __grid_constant_
   const bool nyq_tile = tile >= S::kMainTiles;
   int ky, kz;
   bool valid;
-  V2* base;
+  size_t off;  // element offset of this lane's pencil at x = 0
   size_t stride;
   if (!nyq_tile) {
     const int f = tile * LW + lane;
     valid = f < N * H;
     ky = valid ? f / H : 0;
     kz = valid ? f % H : 0;
-    base = cd.main + (valid ? f : 0);
+    off = valid ? f : 0;
     stride = size_t(N) * H;
   } else {
     ky = (tile - S::kMainTiles) * LW + lane;
     valid = ky < N;
     if (!valid) ky = 0;
     kz = H;
-    base = cd.nyq + ky;
+    off = ky;
     stride = N;
+  }
+  V2* base = (nyq_tile ? cd.nyq : cd.main) + off;
+  const V2* base_in = base;
+  const V2* base2 = nullptr;
+  if constexpr (kAdj) {
+    base_in = (nyq_tile ? cd.nyq_in : cd.main_in) + off;
+    base2 = (nyq_tile ? cd.nyq2 : cd.main2) + off;
   }
 
   // Stage F1: DFT_Q over q of x[p + P q], twiddle W_N^{p v}, to slot p*Q + v.
   for (int it = threadIdx.x; it < LW * P; it += NT) {
     const int p = it / LW;
-    cx<T> v[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) v[q] = valid ? ldc<T>(base + size_t(p + P * q) * stride) : cx<T>{T(0), T(0)};
-    Dft<Q, -1, T>::run(v);
     cx<T> w[Q];
     ld_tw_row<T, Q>(a.tw + TL::kCpv + p * Q, w);
 #pragma unroll
-    for (int vq = 0; vq < Q; ++vq) stc<T>(xs + (p * Q + vq) * LW + lane, vq == 0 ? v[vq] : cmul(v[vq], w[vq]));
+    for (int inp = 0; inp < (kAdj ? 2 : 1); ++inp) {
+      const V2* src = inp == 0 ? base_in : base2;
+      V2* dst = inp == 0 ? xs : xs2;
+      cx<T> v[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) v[q] = valid ? ldc<T>(src + size_t(p + P * q) * stride) : cx<T>{T(0), T(0)};
+      Dft<Q, -1, T>::run(v);
+#pragma unroll
+      for (int vq = 0; vq < Q; ++vq) stc<T>(dst + (p * Q + vq) * LW + lane, vq == 0 ? v[vq] : cmul(v[vq], w[vq]));
+    }
   }
   __syncthreads();
 
@@ -228,12 +325,25 @@ __global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const __grid_constant_
     Dft<P, -1, T>::run(X);
 #pragma unroll
     for (int u = 0; u < P; ++u) stc<T>(xs + (u * Q + vq) * LW + lane, X[u]);
+    if constexpr (kAdj) {
+#pragma unroll
+      for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs2 + (p * Q + vq) * LW + lane);
+      Dft<P, -1, T>::run(X);
+#pragma unroll
+      for (int u = 0; u < P; ++u) stc<T>(xs2 + (u * Q + vq) * LW + lane, X[u]);
+    }
 #pragma unroll 1
     for (int u = 0; u < P; ++u) {
       V2* slot = xs + (u * Q + vq) * LW + lane;
       int bin;
       T sg, ch;
-      const cx<T> y = draw_mode<T, N>(ldc<T>(slot), Q * u + vq, ky, kz, valid, cd, sweep, k0, k1, cid, bin, sg, ch);
+      cx<T> y;
+      if constexpr (!kAdj) {
+        y = draw_mode<T, N>(ldc<T>(slot), Q * u + vq, ky, kz, valid, cd, sweep, k0, k1, cid, bin, sg, ch);
+      } else {
+        y = adjoint_mode<T, N, MODE>(ldc<T>(slot), ldc<T>(xs2 + (u * Q + vq) * LW + lane), Q * u + vq, ky, kz,
+                                     valid, cd, sweep, k0, k1, cid, bin, sg, ch);
+      }
       stc<T>(slot, y);
       shell_accumulate<T>(sg, ch, bin, accw, lane);
     }
@@ -247,7 +357,8 @@ __global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const __grid_constant_
   }
   __syncthreads();
 
-  // Stage I2: IDFT_Q over v of slot p*Q + v, out to x = p + P q.
+  // Stage I2: IDFT_Q over v of slot p*Q + v, out to x = p + P q (adjoint
+  // passes write the adjoint state, held in main/nyq).
   for (int it = threadIdx.x; it < LW * P; it += NT) {
     const int p = it / LW;
     cx<T> v[Q];

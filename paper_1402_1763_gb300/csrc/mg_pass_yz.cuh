@@ -27,6 +27,8 @@ enum PassYZMode : int {
   kModeSweep = 0,        // inverse -> messenger draw -> forward (the hot path)
   kModeMaterialize = 1,  // inverse only, write s to ChainDev::s_out
   kModeLoad = 2,         // read s from ChainDev::s_in, forward only
+  kModeAdjoint = 3,      // adjoint of the messenger step: inverse -> lam_t;
+                         // dd += gamma lam_t; b lam_t -> forward
 };
 
 template <typename T, int N, int C>
@@ -252,6 +254,19 @@ __global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const __grid_constant
         const T sc = T(1.0 / (double(N) * double(N)));
         Z0[q] = {si[0] * sc, si[1] * sc};
         Z1[q] = {si[2] * sc, si[3] * sc};
+      } else if constexpr (MODE == kModeAdjoint) {
+        // t = c + b s + sd g with c = gamma d: d receives gamma lam_t, s
+        // receives b lam_t (the transposes of the per-voxel affine map).
+        cx<T> bcv[4];
+        ld_tw_row<T, 4>(cd.bc + i0, bcv);
+        T* dd = cd.dd + i0;
+        const T* gm = cd.gamma + i0;
+        dd[0] += gm[0] * Z0[q].re;
+        dd[1] += gm[1] * Z0[q].im;
+        dd[2] += gm[2] * Z1[q].re;
+        dd[3] += gm[3] * Z1[q].im;
+        Z0[q] = {bcv[0].re * Z0[q].re, bcv[1].re * Z0[q].im};
+        Z1[q] = {bcv[2].re * Z1[q].re, bcv[3].re * Z1[q].im};
       } else {
         const u32x4 w = philox4x32_10(uint32_t(i0 >> 2), sweep, cid, kStreamMessenger, k0, k1);
         T g0, g1, g2, g3;

@@ -50,6 +50,8 @@ cudaError_t run_mode(int mode, const LaunchArgs<T>& args, cudaStream_t st) {
       return run<T, N, C, kModeMaterialize>(args, st);
     case kModeLoad:
       return run<T, N, C, kModeLoad>(args, st);
+    case kModeAdjoint:
+      return run<T, N, C, kModeAdjoint>(args, st);
     default:
       return cudaErrorInvalidValue;
   }
