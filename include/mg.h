@@ -198,6 +198,30 @@ void mg_destroy(mg_ctx* ctx);
 mg_status mg_philox(uint64_t seed, uint32_t ctr0, uint32_t ctr1, uint32_t ctr2, uint32_t ctr3,
                     int64_t n_calls, uint32_t* out_device, void* stream);
 
+/* Shell sums of a given half-complex spectrum without allocating anything on
+ * the device.  The paper has no counterpart: this exists for callers that
+ * cannot allocate device memory when they need the shell power of a sample —
+ * code under an exhausted memory-pool budget, real-time pipelines that forbid
+ * allocation (and the synchronisation it implies) after start-up, or host code
+ * between kernels it does not own.
+ *   s_hat: device array of n*n*(n/2+1) complex values (interleaved re, im;
+ *          double if precision == 64, float if 32) in the layout [kx][ky][kz],
+ *          kz in [0, n/2] — the unitary convention s_hat = DFT(s)/sqrt(n^3).
+ *   n: even, 4 <= n <= 4096;  n_bins: linear shells on [0, k_Nyq) as in
+ *          mg_init with k_edges == NULL, plus the overflow shell n_bins.
+ *   sigma_out: device, n_bins+1 doubles: sum over the shell of w |s_hat|^2
+ *          (w = 2 for 0 < kz < n/2, 1 on the kz = 0 and n/2 planes; DC excluded).
+ *   nmodes_out: device, n_bins+1 doubles (sum of w), or NULL.
+ *   stream: cudaStream_t or NULL; the call is asynchronous on it.
+ * Scratch: a fixed file-scope device array of 256 x 255 x 2 doubles (1 MiB)
+ * that every GPU loading the library holds until exit; n_bins > 254 does not
+ * fit and returns MG_EINVAL (mg_last_error(NULL) says why).  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) — make
+ * that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (other streams, other threads) race. */
+mg_status mg_shell_sums_noalloc(const void* s_hat, int32_t precision, int32_t n, int32_t n_bins,
+                                double* sigma_out, double* nmodes_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

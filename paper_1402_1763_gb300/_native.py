@@ -82,6 +82,7 @@ def library():
         "mg_destroy": (None, [_P]),
         "mg_philox": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int64,
                                 _P, _P]),
+        "mg_shell_sums_noalloc": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -388,3 +389,12 @@ class Sampler:
             self.close()
         except Exception:
             pass
+
+
+def mg_shell_sums_noalloc(s_hat_ptr: int, precision: int, n: int, n_bins: int, sigma_ptr: int,
+                          nmodes_ptr: int = 0, stream: int = 0):
+    """Shell sums of a device half-complex spectrum into device buffers, with
+    no device allocation (see include/mg.h)."""
+    _check(library().mg_shell_sums_noalloc(C.c_void_p(s_hat_ptr), int(precision), int(n), int(n_bins),
+                                           C.c_void_p(sigma_ptr), C.c_void_p(nmodes_ptr or None),
+                                           C.c_void_p(stream or None)))

@@ -802,6 +802,7 @@ bool valid_chain(const mg_ctx* c, int32_t chain) { return chain >= 0 && size_t(c
 
 namespace mg {
 bool supported_n(int n) { return is_supported_n(n); }
+void set_thread_error(const char* msg) { g_create_error = msg; }
 
 int yz_cluster_choices(int n, int precision, int* out, int max_out) {
   std::vector<int> v;
@@ -1105,7 +1106,7 @@ mg_status mg_sync(mg_ctx* c) {
 }
 
 const char* mg_last_error(const mg_ctx* c) {
-  if (!c) return g_create_error.empty() ? "null context" : g_create_error.c_str();
+  if (!c) return g_create_error.empty() ? "null context" : g_create_error.c_str();  // init and no-context calls
   return c->err.c_str();
 }
 
