@@ -52,16 +52,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def algorithmic_bytes(n: int, chains: int, esz: int):
-    """Bytes one launch of each pass must move ('Algorithmic bytes').
+def algorithmic_bytes(n: int, chains: int, esz: int, n_observed: int):
+    """Bytes one launch of each pass must move.
 
     State per chain: n*n*(n/2) + n*n complex values, each pass reads and writes
-    it once.  The messenger constants (b, c) are one complex value per voxel,
-    read once per pass-YZ launch and shared by every chain of the data set.
+    it once.  The messenger constants (b, c) are one complex value per observed
+    voxel (unobserved voxels have b = 1, c = 0 and need none), read once per
+    pass-YZ launch and shared by every chain of the data set.
     """
     cplx = 2 * esz
     state = (n * n * (n // 2) + n * n) * cplx
-    yz = chains * 2 * state + n ** 3 * cplx
+    yz = chains * 2 * state + n_observed * cplx
     x = chains * 2 * state
     return yz, x
 
@@ -228,7 +229,7 @@ def main():
 
     # per-pass breakdown over the same number of sweeps (CUDA events per pass)
     per = smp.sweep_timed(args.steps) / args.steps
-    yz_bytes, x_bytes = algorithmic_bytes(N_GRID, N_CHAINS, 4)
+    yz_bytes, x_bytes = algorithmic_bytes(N_GRID, N_CHAINS, 4, int((m.R > 0).sum()))
     peak, peak_kind = measured_peaks()
     kern = {"pass_yz": (per[0], yz_bytes), "pass_x": (per[1], x_bytes)}
     dom = max(kern, key=lambda k: kern[k][0])

@@ -38,7 +38,7 @@ struct Group {
   double tau = 0;
   size_t M = 0;
   std::vector<long long> n_b;  // B+1
-  std::shared_ptr<DevBuf> bc, bin_of_m2, n_b_dev, gamma;
+  std::shared_ptr<DevBuf> bc, bin_of_m2, n_b_dev, gamma, row_info, bc_rows;
 };
 
 struct Chain {
@@ -223,6 +223,8 @@ mg_status upload_descriptors(mg_ctx* c) {
       d.main = static_cast<V2*>(ch.main->p);
       d.nyq = static_cast<V2*>(ch.nyq->p);
       d.bc = static_cast<const V2*>(g.bc->p);
+      d.row_info = static_cast<const uint2*>(g.row_info->p);
+      d.bc_rows = static_cast<const V2*>(g.bc_rows->p);
       d.coef = static_cast<const V2*>(ch.coef->p);
       d.partial = static_cast<double*>(ch.partial->p);
       d.bin_of_m2 = static_cast<const uint8_t*>(g.bin_of_m2->p);
@@ -652,6 +654,36 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
         static_cast<const double*>(dN->p), static_cast<const double*>(dR->p), static_cast<const double*>(dd->p), g.M,
         g.tau, static_cast<V2*>(g.bc->p), static_cast<T*>(g.gamma->p));
     MG_CUDA(c, cudaGetLastError());
+    // compact row store of the messenger constants (observed z-ranges only)
+    {
+      const double* Rh = R[gi];
+      const int n = g.n;
+      std::vector<uint32_t> ri(size_t(2) * n * n);
+      uint32_t off = 0;
+      for (size_t row = 0; row < size_t(n) * n; ++row) {
+        int lo = n, hi = 0;
+        for (int z = 0; z < n; ++z)
+          if (Rh[row * n + z] > 0) {
+            lo = std::min(lo, z);
+            hi = z + 1;
+          }
+        if (hi <= lo) lo = hi = 0;
+        lo &= ~3;
+        hi = (hi + 3) & ~3;
+        ri[2 * row] = off;
+        ri[2 * row + 1] = uint32_t(lo) | (uint32_t(hi) << 16);
+        off += uint32_t(hi - lo);
+      }
+      g.row_info = dalloc(ri.size() * sizeof(uint32_t), &e);
+      MG_CUDA(c, e);
+      MG_CUDA(c, cudaMemcpy(g.row_info->p, ri.data(), ri.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+      g.bc_rows = dalloc(size_t(std::max<uint32_t>(off, 4)) * sizeof(V2), &e);
+      MG_CUDA(c, e);
+      pack_rows_kernel<T><<<1024, 256, 0, c->stream>>>(static_cast<const V2*>(g.bc->p),
+                                                       static_cast<const uint2*>(g.row_info->p), n,
+                                                       static_cast<V2*>(g.bc_rows->p));
+      MG_CUDA(c, cudaGetLastError());
+    }
     // shells
     const auto tab = build_bin_table(g.n, g.L, g.B, edges, &g.n_b);
     g.bin_of_m2 = dalloc(tab.size(), &e);
@@ -807,7 +839,7 @@ void set_thread_error(const char* msg) { g_create_error = msg; }
 int yz_cluster_choices(int n, int precision, int* out, int max_out) {
   std::vector<int> v;
   if (precision == 32) {
-    if (n == 256) v = {4, 2};
+    if (n == 256) v = {4, 2, 8};
     else if (n == 192) v = {1, 2};
     else if (n == 128) v = {1, 2};
     else v = {1};
@@ -1036,14 +1068,21 @@ mg_status mg_set_data(mg_ctx* c, int32_t group, const double* d) {
   auto dd = dalloc(g.M * sizeof(double), &e);
   MG_CUDA(c, e);
   MG_CUDA(c, cudaMemcpyAsync(dd->p, d, g.M * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  if (c->precision == 32)
+  if (c->precision == 32) {
     set_data_kernel<float><<<1024, 256, 0, c->stream>>>(static_cast<const float*>(g.gamma->p),
                                                         static_cast<const double*>(dd->p), g.M,
                                                         static_cast<float2*>(g.bc->p));
-  else
+    pack_rows_kernel<float><<<1024, 256, 0, c->stream>>>(static_cast<const float2*>(g.bc->p),
+                                                         static_cast<const uint2*>(g.row_info->p), g.n,
+                                                         static_cast<float2*>(g.bc_rows->p));
+  } else {
     set_data_kernel<double><<<1024, 256, 0, c->stream>>>(static_cast<const double*>(g.gamma->p),
                                                          static_cast<const double*>(dd->p), g.M,
                                                          static_cast<double2*>(g.bc->p));
+    pack_rows_kernel<double><<<1024, 256, 0, c->stream>>>(static_cast<const double2*>(g.bc->p),
+                                                          static_cast<const uint2*>(g.row_info->p), g.n,
+                                                          static_cast<double2*>(g.bc_rows->p));
+  }
   MG_CUDA(c, cudaGetLastError());
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
   return check_status(c);

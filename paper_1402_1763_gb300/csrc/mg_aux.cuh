@@ -76,6 +76,18 @@ __global__ void messenger_constants_kernel(const double* __restrict__ N, const d
   }
 }
 
+// Copy each row's observed z-range of (b, c) into the compact row store.
+template <typename T>
+__global__ void pack_rows_kernel(const typename VT<T>::c2* __restrict__ bc, const uint2* __restrict__ row_info,
+                                 int n, typename VT<T>::c2* __restrict__ bc_rows) {
+  const size_t M = size_t(n) * n * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < M; i += size_t(gridDim.x) * blockDim.x) {
+    const uint2 ri = row_info[i / n];
+    const uint32_t z = uint32_t(i % n), lo = ri.y & 0xffffu, hi = ri.y >> 16;
+    if (z >= lo && z < hi) bc_rows[ri.x + (z - lo)] = bc[i];
+  }
+}
+
 // New data d: c = gamma d (b does not depend on d).
 template <typename T>
 __global__ void set_data_kernel(const T* __restrict__ gamma, const double* __restrict__ d, size_t M,

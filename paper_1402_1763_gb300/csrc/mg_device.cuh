@@ -41,12 +41,19 @@ enum : int { kStNumeric = 1, kStTimeout = 2, kStBadInput = 4, kStNoObserved = 8 
 //   nyq[x][ky]                      complex: the kz = n/2 plane, same form
 // Group data (shared by all chains of one data set):
 //   bc[x][y][z]     (b, c) of the messenger draw t = c + b s + sqrt(tau b) g
+//   row_info[x][y]  (offset, lo | hi << 16): the z-range [lo, hi) of the row
+//                   that holds observed voxels (lo, hi multiples of 4), and
+//                   where it starts in bc_rows; unobserved voxels have b = 1,
+//                   c = 0 and are not stored there
+//   bc_rows[]       (b, c) of those ranges, row after row
 //   bin_of_m2[m^2]  shell id of a mode with |m|^2 = m^2 (B = overflow shell)
 template <typename T>
 struct ChainDev {
   typename VT<T>::c2* main;
   typename VT<T>::c2* nyq;
   const typename VT<T>::c2* bc;
+  const uint2* row_info;
+  const typename VT<T>::c2* bc_rows;
   const typename VT<T>::c2* coef;  // [B+2]: (a / M, sd / sqrt(M)) per shell; [B+1] = DC
   double* partial;                 // [tiles][B+1][2]: per-tile (sigma_b, X_b)
   const uint8_t* bin_of_m2;

@@ -236,10 +236,37 @@ __global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const __grid_constant
       Dft<Q2, +1, T>::run(Z0);
       Dft<Q2, +1, T>::run(Z1);
     }
+    // Messenger constants: only the row's observed z-range is stored; a
+    // group of four voxels outside it has b = 1, c = 0 and needs no load.
+    // Each group's constants are loaded one iteration ahead.
+    uint32_t lo = 0, hi = 0;
+    const typename VT<T>::c2* brow = nullptr;
+    if constexpr (MODE == kModeSweep) {
+      const uint2 ri = __ldg(cd.row_info + size_t(x) * N + y);
+      lo = ri.y & 0xffffu;
+      hi = ri.y >> 16;
+      brow = cd.bc_rows + ri.x;
+    }
+    auto load_group = [&](int z, cx<T>* out) {
+      if (uint32_t(z) >= lo && uint32_t(z) < hi) {
+        ld_tw_row<T, 4>(brow + (z - int(lo)), out);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] = {T(1), T(0)};
+      }
+    };
+    cx<T> bc_next[4];
+    if constexpr (MODE == kModeSweep) load_group(2 * pp, bc_next);
 #pragma unroll
     for (int q = 0; q < Q2; ++q) {
       const int z0 = 2 * (pp + P2 * q);  // voxels z0 .. z0+3
       const size_t i0 = vox_row + z0;
+      cx<T> bcv[4];
+      if constexpr (MODE == kModeSweep) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) bcv[k] = bc_next[k];
+        if (q + 1 < Q2) load_group(2 * (pp + P2 * (q + 1)), bc_next);
+      }
       if constexpr (MODE == kModeMaterialize) {
         T* o = cd.s_out + i0;
         o[0] = Z0[q].re;
@@ -257,7 +284,6 @@ __global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const __grid_constant
       } else if constexpr (MODE == kModeAdjoint) {
         // t = c + b s + sd g with c = gamma d: d receives gamma lam_t, s
         // receives b lam_t (the transposes of the per-voxel affine map).
-        cx<T> bcv[4];
         ld_tw_row<T, 4>(cd.bc + i0, bcv);
         T* dd = cd.dd + i0;
         const T* gm = cd.gamma + i0;
@@ -272,8 +298,6 @@ __global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const __grid_constant
         T g0, g1, g2, g3;
         normal_pair<T>(w.x, w.y, g0, g1);
         normal_pair<T>(w.z, w.w, g2, g3);
-        cx<T> bcv[4];
-        ld_tw_row<T, 4>(cd.bc + i0, bcv);  // (b, c) of the four voxels, vector loads
         const cx<T> bc0 = bcv[0], bc1 = bcv[1], bc2 = bcv[2], bc3 = bcv[3];
         Z0[q].re = bc0.im + bc0.re * Z0[q].re + sqrt(tau * bc0.re) * g0;
         Z0[q].im = bc1.im + bc1.re * Z0[q].im + sqrt(tau * bc1.re) * g1;

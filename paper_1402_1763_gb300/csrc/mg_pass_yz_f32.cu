@@ -22,6 +22,7 @@ cudaError_t launch_pass_yz<float>(int n, int C, int mode, const LaunchArgs<float
   MG_CASE(192, 2)
   MG_CASE(256, 2)
   MG_CASE(256, 4)
+  MG_CASE(256, 8)
 #undef MG_CASE
   return cudaErrorInvalidValue;
 }
