@@ -80,9 +80,17 @@ typedef struct {
   int64_t timeout_cycles; /* budget of device-side waits in clock cycles;
                              0 = library default.                            */
   void* cuda_stream;      /* cudaStream_t the context enqueues on, or NULL.   */
-  int32_t yz_cluster;     /* CTAs per x-plane in the y/z pass (1, 2 or 4) for
-                             every grid size; 0 = the tuned default.  Sizes
-                             the build does not provide give MG_EUNSUPPORTED.*/
+  int32_t yz_cluster;     /* CTAs per x-plane in the y/z pass (1, 2, 4 or 8)
+                             for every grid size; 0 = the default.  Sizes the
+                             build does not provide give MG_EUNSUPPORTED.    */
+  int32_t persistent;     /* nonzero: advance all chains of a batch in ONE
+                             persistent kernel launch per sweep (grid sizes
+                             16..128, at most 6 sizes and 64 chains per size);
+                             MG_EUNSUPPORTED otherwise.  Default 0.          */
+  int32_t autotune;       /* nonzero: at init, time the schedules the build
+                             provides (y/z cluster size per grid size, the
+                             persistent launch) on the context's own chains
+                             and keep the fastest (see mg_tune).  Default 0. */
 } mg_options;
 
 /* Chain statistics (mg_read_stats). Arrays are caller-owned with the sizes
@@ -189,6 +197,20 @@ const char* mg_last_error(const mg_ctx* ctx);
 
 /* Free everything the context owns; ctx may be NULL. */
 void mg_destroy(mg_ctx* ctx);
+
+/* Autotuner: time every schedule the build provides for this context — the
+ * y/z pass's cluster size per grid size and, where eligible, the persistent
+ * one-launch sweep against one launch per pass — with `reps` sweeps each on
+ * the context's own chains (their state, P and the sweep counter are saved
+ * and restored, so the chains are unaffected), then keep the fastest.  The
+ * choice is cached per GPU model and batch shape for later contexts in this
+ * process.  Synchronises. */
+mg_status mg_tune(mg_ctx* ctx, int32_t reps);
+
+/* The schedule in use: number of grid sizes, and per size its n, y/z cluster
+ * size; *persistent is 1 if the sweep is one persistent launch.  Arrays hold
+ * at least 8 entries; any pointer may be NULL. */
+mg_status mg_schedule(mg_ctx* ctx, int32_t* n_sizes, int32_t* n, int32_t* yz_cluster, int32_t* persistent);
 
 /* Raw Philox4x32-10 words on the device (Salmon et al. 2011; the per-core
  * generators of Sec. 3.4): for i in [0, n_calls), call i uses counter

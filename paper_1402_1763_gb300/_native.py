@@ -27,7 +27,7 @@ class MgOptions(C.Structure):
                 ("tau_scale", C.c_double), ("P0", C.POINTER(C.c_double)),
                 ("record_every", C.c_int32), ("fix_P", C.c_int32),
                 ("timeout_cycles", C.c_int64), ("cuda_stream", C.c_void_p),
-                ("yz_cluster", C.c_int32)]
+                ("yz_cluster", C.c_int32), ("persistent", C.c_int32), ("autotune", C.c_int32)]
 
 
 class MgStats(C.Structure):
@@ -72,6 +72,9 @@ def library():
         "mg_set_s": (C.c_int, [_P, C.c_int32, _P, C.c_int32]),
         "mg_set_pk": (C.c_int, [_P, C.c_int32, _D]),
         "mg_set_data": (C.c_int, [_P, C.c_int32, _D]),
+        "mg_tune": (C.c_int, [_P, C.c_int32]),
+        "mg_schedule": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_int32)]),
         "mg_adjoint": (C.c_int, [_P, C.c_int32, C.c_int32, _D, _D, _D, _D, _D]),
         "mg_get_sweep_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
         "mg_set_sweep_count": (C.c_int, [_P, C.c_int64]),
@@ -217,6 +220,19 @@ def mg_adjoint(ctx, chain: int, K: int, logP, w):
     return float(L[0]), gl, gd.reshape(n, n, n)
 
 
+def mg_tune(ctx, reps: int = 5):
+    _check(library().mg_tune(ctx, int(reps)), ctx)
+
+
+def mg_schedule(ctx) -> dict:
+    ns, pers = C.c_int32(), C.c_int32()
+    n = (C.c_int32 * 8)()
+    cl = (C.c_int32 * 8)()
+    _check(library().mg_schedule(ctx, C.byref(ns), n, cl, C.byref(pers)), ctx)
+    return {"sizes": [n[i] for i in range(ns.value)], "yz_cluster": [cl[i] for i in range(ns.value)],
+            "persistent": bool(pers.value)}
+
+
 def mg_get_sweep_count(ctx) -> int:
     v = C.c_int64()
     _check(library().mg_get_sweep_count(ctx, C.byref(v)), ctx)
@@ -268,7 +284,7 @@ class Sampler:
 
     @staticmethod
     def _opts(precision, n_chains, chain_id0, tau_scale, P0, record_every, fix_P, stream,
-              yz_cluster=0):
+              yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0):
         o = mg_options_init()
         o.precision = int(precision)
         o.n_chains = int(n_chains)
@@ -282,14 +298,17 @@ class Sampler:
         o.fix_P = int(bool(fix_P))
         o.cuda_stream = stream or None
         o.yz_cluster = int(yz_cluster)
+        o.persistent = int(bool(persistent))
+        o.autotune = int(bool(autotune))
+        o.timeout_cycles = int(timeout_cycles)
         return o, keep
 
     @classmethod
     def single(cls, n, L, N, R, d, n_bins, seed, precision=64, n_chains=1, chain_id0=0,
                tau_scale=1.0, P0=None, record_every=0, fix_P=False, k_edges=None, stream=0,
-               yz_cluster=0):
+               yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0):
         o, keep = cls._opts(precision, n_chains, chain_id0, tau_scale, P0, record_every, fix_P, stream,
-                            yz_cluster)
+                            yz_cluster, persistent, autotune, timeout_cycles)
         ctx = mg_init(n, L, N, R, d, n_bins, seed, o, k_edges)
         del keep
         return cls(ctx, precision)
@@ -297,9 +316,9 @@ class Sampler:
     @classmethod
     def batch(cls, ns, Ls, Ns, Rs, ds, n_bins, seeds, precision=32, n_chains=1, chain_id0=0,
               tau_scale=1.0, P0=None, record_every=0, fix_P=False, k_edges=None, stream=0,
-              yz_cluster=0):
+              yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0):
         o, keep = cls._opts(precision, n_chains, chain_id0, tau_scale, P0, record_every, fix_P, stream,
-                            yz_cluster)
+                            yz_cluster, persistent, autotune, timeout_cycles)
         ctx = mg_init_batch(ns, Ls, Ns, Rs, ds, n_bins, seeds, o, k_edges)
         del keep
         return cls(ctx, precision)
@@ -358,6 +377,12 @@ class Sampler:
 
     def set_pk(self, chain, P):
         mg_set_pk(self.ctx, chain, _f64(P))
+
+    def tune(self, reps=5):
+        mg_tune(self.ctx, reps)
+
+    def schedule(self) -> dict:
+        return mg_schedule(self.ctx)
 
     def set_data(self, group, d):
         mg_set_data(self.ctx, group, d)

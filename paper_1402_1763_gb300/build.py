@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libmg.so")
-SOURCES = ["mg_pass_yz_f32.cu", "mg_pass_yz_f64.cu", "mg_pass_x.cu", "mg_api.cu", "mg_noalloc.cu"]
+SOURCES = ["mg_pass_yz_f32.cu", "mg_pass_yz_f64.cu", "mg_pass_x.cu", "mg_api.cu", "mg_noalloc.cu", "mg_persist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -15,6 +15,9 @@
 #include "../../include/mg.h"
 #include "mg_aux.cuh"
 #include "mg_launch.h"
+#include "mg_persist.h"
+
+#include <mutex>
 
 using namespace mg;
 
@@ -78,6 +81,12 @@ struct mg_ctx {
   std::string err;
   cudaGraphExec_t graph = nullptr;
   bool graph_failed = false;
+  // persistent one-launch sweep
+  bool persist = false;
+  std::vector<char> persist_args;  // PersistArgs<T>
+  std::shared_ptr<DevBuf> persist_ctr;
+  int persist_grid = 0;
+  long long timeout = 0;
 };
 
 namespace {
@@ -312,8 +321,215 @@ mg_status enqueue_passes(mg_ctx* c, int which) {
   return MG_OK;
 }
 
+bool persist_eligible(const mg_ctx* c) {
+  if (c->classes.empty() || c->classes.size() > size_t(kMaxPersistClasses)) return false;
+  for (const auto& sc : c->classes)
+    if (!persist_supports(sc.n) || sc.C != 1 || sc.chains.size() > size_t(kMaxLaunchChains)) return false;
+  return true;
+}
+
+// Build the persistent launch's parameters (queue layout, chain numbering).
+template <typename T>
+mg_status build_persist(mg_ctx* c) {
+  PersistArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.ncls = int(c->classes.size());
+  int u = 0;
+  for (int k = 0; k < a.ncls; ++k) {
+    const SizeClass& sc = c->classes[k];
+    a.cls[k] = *reinterpret_cast<const LaunchArgs<T>*>(sc.args[0].data());
+    a.n[k] = sc.n;
+    a.tiles[k] = pass_x_tiles(sc.n);
+    for (size_t i = 0; i < sc.chains.size(); ++i) a.ctx_chain[k][i] = sc.chains[i];
+    a.yz_begin[k] = u;
+    u += sc.n * int(sc.chains.size());
+  }
+  a.yz_begin[a.ncls] = u;
+  for (int k = 0; k < a.ncls; ++k) {
+    a.x_begin[k] = u;
+    u += a.tiles[k] * int(c->classes[k].chains.size());
+  }
+  a.x_begin[a.ncls] = u;
+  a.draw_begin = u;
+  a.n_chains_total = int(c->chains.size());
+  a.total = u + a.n_chains_total;
+  a.fix_P = c->fix_P;
+  a.timeout = c->timeout;
+  cudaError_t e;
+  c->persist_ctr = dalloc(size_t(2 + 2 * a.n_chains_total) * sizeof(unsigned), &e);
+  MG_CUDA(c, e);
+  a.ctr = static_cast<unsigned*>(c->persist_ctr->p);
+  a.draw = static_cast<const DrawDev*>(c->d_draw->p);
+  a.status = static_cast<int*>(c->d_status->p);
+  a.sweep_ctr = static_cast<uint32_t*>(c->d_sweep->p);
+  c->persist_grid = persist_grid<T>(a, c->B_max);
+  if (c->persist_grid <= 0) return fail(c, MG_ECUDA, "persistent kernel does not fit on this GPU");
+  c->persist_args.assign(reinterpret_cast<const char*>(&a), reinterpret_cast<const char*>(&a) + sizeof(a));
+  return MG_OK;
+}
+
+template <typename T>
+mg_status enqueue_persistent(mg_ctx* c) {
+  const auto& a = *reinterpret_cast<const PersistArgs<T>*>(c->persist_args.data());
+  MG_CUDA(c, cudaMemsetAsync(c->persist_ctr->p, 0, size_t(2 + 2 * a.n_chains_total) * sizeof(unsigned), c->stream));
+  MG_CUDA(c, launch_persistent<T>(a, c->B_max, c->persist_grid, c->stream));
+  return MG_OK;
+}
+
 mg_status enqueue_sweep(mg_ctx* c) {
+  if (c->persist) return c->precision == 32 ? enqueue_persistent<float>(c) : enqueue_persistent<double>(c);
   return c->precision == 32 ? enqueue_passes<float>(c, 7) : enqueue_passes<double>(c, 7);
+}
+
+void drop_graph(mg_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  c->graph_failed = false;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: time the schedules the build provides on the context's own
+// chains (state saved and restored around every trial) and keep the fastest.
+// ---------------------------------------------------------------------------
+
+mg_status check_status(mg_ctx* c);
+
+struct Schedule {
+  std::vector<int> C;
+  bool persist = false;
+};
+std::mutex g_tune_mu;
+std::map<std::string, Schedule> g_tune_cache;
+
+std::string tune_key(const mg_ctx* c) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, dev);
+  std::string k = std::string(prop.name) + "|" + std::to_string(c->precision);
+  for (const auto& sc : c->classes) k += "|" + std::to_string(sc.n) + "x" + std::to_string(sc.chains.size());
+  return k;
+}
+
+template <typename T>
+mg_status tune_impl(mg_ctx* c, int reps) {
+  using V2 = typename VT<T>::c2;
+  if (reps < 1) reps = 1;
+  const std::string key = tune_key(c);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      for (size_t k = 0; k < c->classes.size(); ++k) c->classes[k].C = it->second.C[k];
+      c->persist = false;
+      if (it->second.persist) {
+        mg_status st = build_persist<T>(c);
+        if (st != MG_OK) return st;
+        c->persist = true;
+      }
+      drop_graph(c);
+      return MG_OK;
+    }
+  }
+  cudaStream_t s = c->stream;
+  // save every chain's state, P and the sweep counter
+  std::vector<std::shared_ptr<DevBuf>> save(c->chains.size());
+  std::vector<size_t> main_b(c->chains.size()), nyq_b(c->chains.size()), p_b(c->chains.size());
+  cudaError_t e;
+  for (size_t i = 0; i < c->chains.size(); ++i) {
+    const Group& g = c->groups[c->chains[i].group];
+    main_b[i] = size_t(g.n) * g.n * (g.n / 2) * sizeof(V2);
+    nyq_b[i] = size_t(g.n) * g.n * sizeof(V2);
+    p_b[i] = size_t(g.B + 1) * sizeof(double);
+    save[i] = dalloc(main_b[i] + nyq_b[i] + p_b[i], &e);
+    MG_CUDA(c, e);
+    char* d = static_cast<char*>(save[i]->p);
+    MG_CUDA(c, cudaMemcpyAsync(d, c->chains[i].main->p, main_b[i], cudaMemcpyDeviceToDevice, s));
+    MG_CUDA(c, cudaMemcpyAsync(d + main_b[i], c->chains[i].nyq->p, nyq_b[i], cudaMemcpyDeviceToDevice, s));
+    MG_CUDA(c, cudaMemcpyAsync(d + main_b[i] + nyq_b[i], c->chains[i].P->p, p_b[i], cudaMemcpyDeviceToDevice, s));
+  }
+  uint32_t sw0 = 0;
+  MG_CUDA(c, cudaMemcpyAsync(&sw0, c->d_sweep->p, sizeof(sw0), cudaMemcpyDeviceToHost, s));
+  MG_CUDA(c, cudaStreamSynchronize(s));
+  auto restore = [&]() -> mg_status {
+    for (size_t i = 0; i < c->chains.size(); ++i) {
+      const char* d = static_cast<const char*>(save[i]->p);
+      MG_CUDA(c, cudaMemcpyAsync(c->chains[i].main->p, d, main_b[i], cudaMemcpyDeviceToDevice, s));
+      MG_CUDA(c, cudaMemcpyAsync(c->chains[i].nyq->p, d + main_b[i], nyq_b[i], cudaMemcpyDeviceToDevice, s));
+      MG_CUDA(c, cudaMemcpyAsync(c->chains[i].P->p, d + main_b[i] + nyq_b[i], p_b[i], cudaMemcpyDeviceToDevice, s));
+    }
+    MG_CUDA(c, cudaMemcpyAsync(c->d_sweep->p, &sw0, sizeof(sw0), cudaMemcpyHostToDevice, s));
+    mg_status st = launch_shell_draw<T>(c, 0, false);
+    if (st != MG_OK) return st;
+    MG_CUDA(c, cudaStreamSynchronize(s));
+    return MG_OK;
+  };
+  cudaEvent_t e0, e1;
+  MG_CUDA(c, cudaEventCreate(&e0));
+  MG_CUDA(c, cudaEventCreate(&e1));
+  auto elapsed = [&](float* ms) -> mg_status {
+    MG_CUDA(c, cudaEventSynchronize(e1));
+    MG_CUDA(c, cudaEventElapsedTime(ms, e0, e1));
+    return MG_OK;
+  };
+  mg_status st = MG_OK;
+  // 1. the y/z cluster size of each grid size, timing that pass alone
+  for (auto& sc : c->classes) {
+    int cand[4];
+    const int nc = yz_cluster_choices(sc.n, c->precision, cand, 4);
+    float best = 1e30f;
+    int bestC = sc.C;
+    for (int i = 0; i < nc; ++i) {
+      LaunchArgs<T> none;
+      std::memset(&none, 0, sizeof(none));
+      MG_CUDA(c, launch_pass_yz<T>(sc.n, cand[i], 0, none, s));
+      const LaunchArgs<T>& la = *reinterpret_cast<const LaunchArgs<T>*>(sc.args[0].data());
+      for (auto& blob : sc.args)  // warm-up
+        MG_CUDA(c, launch_pass_yz<T>(sc.n, cand[i], 0, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()), s));
+      (void)la;
+      MG_CUDA(c, cudaEventRecord(e0, s));
+      for (int r = 0; r < reps; ++r)
+        for (auto& blob : sc.args)
+          MG_CUDA(c, launch_pass_yz<T>(sc.n, cand[i], 0, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()), s));
+      MG_CUDA(c, cudaEventRecord(e1, s));
+      float ms = 0.f;
+      if ((st = elapsed(&ms)) != MG_OK) return st;
+      if (ms < best) {
+        best = ms;
+        bestC = cand[i];
+      }
+      if ((st = restore()) != MG_OK) return st;
+    }
+    sc.C = bestC;
+  }
+  // 2. one persistent launch per sweep against one launch per pass
+  c->persist = false;
+  bool use_persist = false;
+  if (persist_eligible(c)) {
+    if ((st = build_persist<T>(c)) != MG_OK) return st;
+    float t[2];
+    for (int mode = 0; mode < 2; ++mode) {
+      c->persist = mode == 1;
+      if ((st = enqueue_sweep(c)) != MG_OK) return st;  // warm-up
+      MG_CUDA(c, cudaEventRecord(e0, s));
+      for (int r = 0; r < reps; ++r)
+        if ((st = enqueue_sweep(c)) != MG_OK) return st;
+      MG_CUDA(c, cudaEventRecord(e1, s));
+      if ((st = elapsed(&t[mode])) != MG_OK) return st;
+      if ((st = restore()) != MG_OK) return st;
+    }
+    use_persist = t[1] < t[0];
+  }
+  c->persist = use_persist;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  drop_graph(c);
+  Schedule sch;
+  for (const auto& sc : c->classes) sch.C.push_back(sc.C);
+  sch.persist = use_persist;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = sch;
+  return check_status(c);
 }
 
 // Launch arguments for one chain with an input or output field pointer attached.
@@ -769,6 +985,14 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
   s = launch_shell_draw<T>(c, 0, false);
   if (s != MG_OK) return s;
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (opt->persistent) {
+    if (!persist_eligible(c))
+      return fail(c, MG_EUNSUPPORTED,
+                  "persistent launch needs grid sizes 16..128 without y/z clusters, <= 6 sizes, <= 64 chains each");
+    if ((s = build_persist<T>(c)) != MG_OK) return s;
+    c->persist = true;
+  }
+  if (opt->autotune && (s = tune_impl<T>(c, 5)) != MG_OK) return s;
   return MG_OK;
 }
 
@@ -804,6 +1028,7 @@ mg_status create(mg_ctx** out, int32_t n_groups, const mg_grid* grids, const dou
   c->precision = opt.precision;
   c->fix_P = opt.fix_P ? 1 : 0;
   c->record_every = opt.record_every;
+  c->timeout = opt.timeout_cycles > 0 ? opt.timeout_cycles : 4000000000ll;
   if (opt.cuda_stream) {
     c->stream = static_cast<cudaStream_t>(opt.cuda_stream);
   } else {
@@ -870,6 +1095,8 @@ void mg_options_init(mg_options* o) {
   o->timeout_cycles = 0;
   o->cuda_stream = nullptr;
   o->yz_cluster = 0;
+  o->persistent = 0;
+  o->autotune = 0;
 }
 
 mg_status mg_init(mg_ctx** out, const mg_grid* grid, const double* N, const double* R, const double* d,
@@ -1105,6 +1332,23 @@ mg_status mg_adjoint(mg_ctx* c, int32_t chain, int32_t K, const double* logP, co
   if (s != MG_OK) return s;
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
   return check_status(c);
+}
+
+mg_status mg_tune(mg_ctx* c, int32_t reps) {
+  if (!c) return MG_EINVAL;
+  if (c->sticky != MG_OK) return c->sticky;
+  return c->precision == 32 ? tune_impl<float>(c, reps) : tune_impl<double>(c, reps);
+}
+
+mg_status mg_schedule(mg_ctx* c, int32_t* n_sizes, int32_t* n, int32_t* yz_cluster, int32_t* persistent) {
+  if (!c) return MG_EINVAL;
+  if (n_sizes) *n_sizes = int32_t(c->classes.size());
+  for (size_t k = 0; k < c->classes.size() && k < 8; ++k) {
+    if (n) n[k] = c->classes[k].n;
+    if (yz_cluster) yz_cluster[k] = c->classes[k].C;
+  }
+  if (persistent) *persistent = c->persist ? 1 : 0;
+  return MG_OK;
 }
 
 mg_status mg_get_sweep_count(mg_ctx* c, int64_t* out) {

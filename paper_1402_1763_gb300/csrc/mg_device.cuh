@@ -24,6 +24,14 @@ __device__ __forceinline__ cx<T> ldc(const typename VT<T>::c2* p) {
   const typename VT<T>::c2 v = *p;
   return {v.x, v.y};
 }
+// Load through L2 only: chain state is streamed once per pass, and inside the
+// persistent sweep another SM may have rewritten it since this SM last saw
+// the line, so it must not come from a (non-coherent) L1 copy.
+template <typename T>
+__device__ __forceinline__ cx<T> ldcg(const typename VT<T>::c2* p) {
+  const typename VT<T>::c2 v = __ldcg(p);
+  return {v.x, v.y};
+}
 template <typename T>
 __device__ __forceinline__ void stc(typename VT<T>::c2* p, cx<T> a) {
   typename VT<T>::c2 v;

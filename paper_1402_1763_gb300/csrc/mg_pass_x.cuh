@@ -242,8 +242,10 @@ struct PassXShape {
   }
 };
 
-template <typename T, int N, int NT, int MINB, int MODE = kXSweep>
-__global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const __grid_constant__ LaunchArgs<T> a) {
+// One tile of 32 pencils of one chain (`block` = chain * tiles + tile).
+// Called by pass_x_kernel and by the persistent sweep kernel.
+template <typename T, int N, int NT, int MODE = kXSweep>
+__device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, unsigned char* smem_raw) {
   using S = PassXShape<T, N>;
   using V2 = typename VT<T>::c2;
   using TL = TwLayout<N>;
@@ -251,13 +253,12 @@ __global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const __grid_constant_
   constexpr int NW = NT / 32;
   constexpr bool kAdj = MODE != kXSweep;
   static_assert(NT % 32 == 0, "whole warps");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   V2* xs = reinterpret_cast<V2*>(smem_raw);  // [N][LW], slot p*Q + v
   V2* xs2 = reinterpret_cast<V2*>(smem_raw + S::kXchgBytes);  // adjoint: second input
   T* acc = reinterpret_cast<T*>(smem_raw + (kAdj ? 2 : 1) * S::kXchgBytes);
 
-  const int tile = blockIdx.x % S::kTiles;
-  const int chain = blockIdx.x / S::kTiles;
+  const int tile = block % S::kTiles;
+  const int chain = block / S::kTiles;
   const ChainDev<T> cd = a.chains[chain];
   const uint32_t k0 = a.k0[chain], k1 = a.k1[chain], cid = a.cid[chain];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const __grid_constant_
       V2* dst = inp == 0 ? xs : xs2;
       cx<T> v[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) v[q] = valid ? ldc<T>(src + size_t(p + P * q) * stride) : cx<T>{T(0), T(0)};
+      for (int q = 0; q < Q; ++q) v[q] = valid ? ldcg<T>(src + size_t(p + P * q) * stride) : cx<T>{T(0), T(0)};
       Dft<Q, -1, T>::run(v);
 #pragma unroll
       for (int vq = 0; vq < Q; ++vq) stc<T>(dst + (p * Q + vq) * LW + lane, vq == 0 ? v[vq] : cmul(v[vq], w[vq]));
@@ -396,6 +397,12 @@ __global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const __grid_constant_
       part[2 * b + 1] = s2;
     }
   }
+}
+
+template <typename T, int N, int NT, int MINB, int MODE = kXSweep>
+__global__ void __launch_bounds__(NT, MINB) pass_x_kernel(const __grid_constant__ LaunchArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pass_x_tile<T, N, NT, MODE>(a, int(blockIdx.x), smem_raw);
 }
 
 }  // namespace mg

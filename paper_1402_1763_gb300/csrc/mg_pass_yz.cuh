@@ -80,15 +80,17 @@ __device__ __forceinline__ void cluster_barrier() {
   }
 }
 
-template <typename T, int N, int C, int MODE, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const __grid_constant__ LaunchArgs<T> a) {
+// One x-plane of one chain (`unit` = plane * n_chains + chain), the CTA's part
+// when C > 1.  Called by pass_yz_kernel (one unit per CTA or cluster) and by
+// the persistent sweep kernel (C = 1, units taken from a work queue).
+template <typename T, int N, int C, int MODE, int NT>
+__device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, unsigned char* smem_raw) {
   using S = PassYZShape<T, N, C>;
   using V2 = typename VT<T>::c2;
   using TL = TwLayout<N>;
   const typename VT<T>::c2* __restrict__ tw = a.tw;
   constexpr int H = S::H, P = S::P, Q = S::Q, P2 = S::P2, Q2 = S::Q2;
   constexpr int ROWS = S::ROWS, RS = S::RS, PC = S::PC, QC = S::QC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   V2* rows = reinterpret_cast<V2*>(smem_raw);
   V2* col0 = rows + ROWS * RS;
 
@@ -102,7 +104,6 @@ __global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const __grid_constant
     col0_r0 = map_to_rank(smem_addr(col0), 0u);
   }
   constexpr uint32_t kEl = sizeof(V2);
-  const int unit = blockIdx.x / C;
   const int x = unit / a.n_chains;
   const int chain = unit % a.n_chains;
   const ChainDev<T> cd = a.chains[chain];
@@ -129,11 +130,11 @@ __global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const __grid_constant
           const int l = it % H;
           const int v = int(rank) * QC + it / H;
 #pragma unroll
-          for (int u = 0; u < P; ++u) X[b][u] = ldc<T>(mainp + size_t(Q * u + v) * H + l);
+          for (int u = 0; u < P; ++u) X[b][u] = ldcg<T>(mainp + size_t(Q * u + v) * H + l);
           if (l == 0) {
 #pragma unroll
             for (int u = 0; u < P; ++u) {
-              const cx<T> y = ldc<T>(nyqp + Q * u + v);
+              const cx<T> y = ldcg<T>(nyqp + Q * u + v);
               X[b][u] = {X[b][u].re - y.im, X[b][u].im + y.re};
             }
           }
@@ -429,6 +430,12 @@ __global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const __grid_constant
       stc<T>(nyqp + ky, cmul_i<-1>(cscale(csub(f, g), h)));
     }
   }
+}
+
+template <typename T, int N, int C, int MODE, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) pass_yz_kernel(const __grid_constant__ LaunchArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pass_yz_unit<T, N, C, MODE, NT>(a, int(blockIdx.x) / C, smem_raw);
 }
 
 }  // namespace mg
