@@ -176,6 +176,67 @@ def cpu_baseline(seconds_budget=25.0):
                       "numpy FP64 single-threaded"}
 
 
+def run_other_workload(args):
+    """Secondary workloads (not the headline line): the batching workload in
+    one persistent launch per sweep, the adjoint of 8 sweeps at 128^3 FP32, and
+    the plain FP64 sampler on the 128^3 grid with holes."""
+    import torch
+    from paper_1402_1763_gb300 import Sampler
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    if args.workload == "batch-48chains":
+        w = mockgen.workload(4)
+        g = Sampler.batch([m.n for m in w.mocks], [m.L for m in w.mocks], [m.N for m in w.mocks],
+                          [m.R for m in w.mocks], [m.d for m in w.mocks], [m.n_bins for m in w.mocks], w.seeds,
+                          precision=32, autotune=True, stream=stream.cuda_stream)
+        units = sum(m.n ** 3 for m in w.mocks)
+        g.sweep(args.warmup)
+        g.sync()
+        ev[0].record(stream)
+        g.sweep(args.steps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / args.steps
+        line.update(value=units / (ms * 1e-3), ms_per_step=ms, dtype="f32",
+                    config={"workload": w.name, "schedule": g.schedule(), "chains": len(w.mocks)})
+    elif args.workload == "adjoint-128":
+        w = mockgen.workload(5)
+        m = w.mocks[0]
+        g = Sampler.single(m.n, m.L, m.N, m.R, m.d, m.n_bins, 5, precision=32, stream=stream.cuda_stream)
+        wts = mockgen.mode_weights(m.n, 5)
+        logP = np.log(np.full(m.n_bins + 1, m.L ** 3 / m.n ** 3))
+        for _ in range(args.warmup):
+            g.adjoint(0, 8, logP, wts)
+        t0 = time.perf_counter()
+        reps = max(1, args.steps // 20)
+        for _ in range(reps):
+            g.adjoint(0, 8, logP, wts)
+        dt = (time.perf_counter() - t0) / reps
+        line.update(metric="adjoint of K = 8 fixed-P sweeps (loss + dL/dlogP + dL/dd), wall time",
+                    value=dt * 1e3, unit="ms per call", higher_is_better=False, ms_per_step=dt * 1e3,
+                    dtype="f32", config={"workload": w.name, "K": 8,
+                                         "note": "host buffers in and out; includes per-call allocations"})
+    elif args.workload == "fp64-128holes":
+        w = mockgen.workload(2)
+        m = w.mocks[0]
+        g = Sampler.single(m.n, m.L, m.N, m.R, m.d, m.n_bins, 2, precision=64, stream=stream.cuda_stream)
+        g.sweep(args.warmup)
+        g.sync()
+        ev[0].record(stream)
+        g.sweep(args.steps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / args.steps
+        line.update(value=m.n ** 3 / (ms * 1e-3), ms_per_step=ms, dtype="f64",
+                    config={"workload": w.name, "removed_fraction": m.removed_fraction})
+    g.close()
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,12 +244,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="256-fp32-16chains",
+                    choices=["256-fp32-16chains", "batch-48chains", "adjoint-128", "fp64-128holes"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = replicas.rank_world()
 
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.workload != "256-fp32-16chains":
+        return run_other_workload(args)
 
     import torch
     import torch.distributed as dist
