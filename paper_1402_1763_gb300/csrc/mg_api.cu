@@ -198,7 +198,7 @@ std::vector<typename VT<T>::c2> twiddles(int n) {
   int P, Q, P2, Q2;
   split_of(n, &P, &Q);
   split_of(n / 2, &P2, &Q2);
-  std::vector<typename VT<T>::c2> t(size_t(4) * n);
+  std::vector<typename VT<T>::c2> t(size_t(4) * n + n / 2);
   auto W = [n](long e) {
     const long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)(e % n) / (long double)n;
     typename VT<T>::c2 v;
@@ -216,6 +216,7 @@ std::vector<typename VT<T>::c2> twiddles(int n) {
     for (int p = 0; p < P2; ++p) {
       t[3 * n + v * P2 + p] = W(2L * p * v);
       t[3 * n + n / 2 + p * Q2 + v] = W(2L * p * v);
+      t[4 * n + v * P2 + p] = W(long(Q2) * p + v);
     }
   return t;
 }

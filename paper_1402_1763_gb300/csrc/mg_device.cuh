@@ -105,7 +105,9 @@ struct LaunchArgs {
 template <int N>
 struct TwLayout {
   static constexpr int kLin = 0, kCvp = N, kCpv = 2 * N, kRvp = 3 * N, kRpv = 3 * N + N / 2;
-  static constexpr int kSize = 4 * N;
+  // kLin in column order of the row stages: entry v*P2 + u = W_N^(Q2 u + v)
+  static constexpr int kLinT = 4 * N;
+  static constexpr int kSize = 4 * N + N / 2;
 };
 
 // Load K consecutive complex twiddles (16-byte vector loads where aligned).
@@ -125,6 +127,21 @@ __device__ __forceinline__ void ld_tw_row(const typename VT<T>::c2* __restrict__
       const typename VT<T>::c2 q = __ldg(row + i);
       w[i] = {q.x, q.y};
     }
+  }
+}
+
+// Load two consecutive complex twiddles row[0], row[1] (one 16-byte load in
+// FP32; row must then be 16-byte aligned).
+template <typename T>
+__device__ __forceinline__ void ld_tw2(const typename VT<T>::c2* __restrict__ row, cx<T>& w0, cx<T>& w1) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(row));
+    w0 = {q.x, q.y};
+    w1 = {q.z, q.w};
+  } else {
+    const typename VT<T>::c2 a = __ldg(row), b = __ldg(row + 1);
+    w0 = {a.x, a.y};
+    w1 = {b.x, b.y};
   }
 }
 

@@ -80,6 +80,22 @@ __device__ __forceinline__ void cluster_barrier() {
   }
 }
 
+// A cluster barrier split into its two halves.  The arrive releases this
+// thread's earlier writes (and marks its reads of other CTAs' shared memory
+// as done); the wait acquires the other CTAs' released writes.  Work placed
+// between the two (here: global stores) neither delays the other CTAs nor
+// has to be drained before the arrive.  With C == 1 the pair is one
+// __syncthreads.
+template <int C>
+__device__ __forceinline__ void cluster_arrive() {
+  if constexpr (C > 1) asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+template <int C>
+__device__ __forceinline__ void cluster_wait() {
+  if constexpr (C > 1) asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+  else __syncthreads();
+}
+
 // One x-plane of one chain (`unit` = plane * n_chains + chain), the CTA's part
 // when C > 1.  Called by pass_yz_kernel (one unit per CTA or cluster) and by
 // the persistent sweep kernel (C = 1, units taken from a work queue).
@@ -91,6 +107,10 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
   const typename VT<T>::c2* __restrict__ tw = a.tw;
   constexpr int H = S::H, P = S::P, Q = S::Q, P2 = S::P2, Q2 = S::Q2;
   constexpr int ROWS = S::ROWS, RS = S::RS, PC = S::PC, QC = S::QC;
+  // FP32 folds the real-transform pre/post-processing into the row stages
+  // (two columns of P2 values per thread); in FP64 those registers would
+  // spill, so the pre/post-processing stays a stage of its own there.
+  constexpr bool kFuseRows = sizeof(T) == 4;
   V2* rows = reinterpret_cast<V2*>(smem_raw);
   V2* col0 = rows + ROWS * RS;
 
@@ -175,46 +195,137 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
     }
     __syncthreads();
 
-    // Row pre-processing for the C2R z-transform through a half-length
-    // complex IDFT: Z'[k] = (X[k] + conj X[H-k]) + i W_n^{-k} (X[k] - conj X[H-k]).
-    for (int it = threadIdx.x; it < ROWS * (H / 2 + 1); it += NT) {
-      const int r = it % ROWS;
-      const int k = it / ROWS;
-      V2* row = rows + r * RS;
-      if (k == 0) {
-        const cx<T> z = ldc<T>(row);
-        stc<T>(row, cx<T>{z.re + z.im, z.re - z.im});
-      } else {
-        const int kk = H - k;
-        const cx<T> a = ldc<T>(row + k), b = ldc<T>(row + kk);
-        {
-          const cx<T> e = cadd(a, cconj(b)), d = csub(a, cconj(b));
-          stc<T>(row + k, cadd(e, cmul_i<+1>(cmulc(d, ldc<T>(tw + k)))));
+    if constexpr (kFuseRows) {
+      // Row stage I1 with the C2R pre-processing of the z-transform folded in.
+      // The C2R runs as a half-length complex IDFT of
+      //   Z'[k] = (X[k] + conj X[H-k]) + i W_n^{-k} (X[k] - conj X[H-k]),
+      // Z'[0] = (X0 + X_{n/2}) + i (X0 - X_{n/2}) from the packed column 0.
+      // Element k = Q2 u + v pairs with H - k, which sits in column Q2 - v
+      // (row u' = P2-1-u), or in column 0 itself (u' = P2-u) for v = 0, or in
+      // column Q2/2 itself (u' = P2-1-u).  One item therefore takes the two
+      // columns {v, Q2-v} (item 0: {0, Q2/2}), forms Z' in registers, runs the
+      // IDFT_P2 of each column and twiddles by W_{n/2}^{-p v} into column slots
+      // p*Q2 + v.
+      constexpr int NG = (Q2 + 1) / 2;
+      for (int it = threadIdx.x; it < ROWS * NG; it += NT) {
+        const int r = it % ROWS;
+        const int g = it / ROWS;
+        V2* row = rows + r * RS;
+        const int va = g;
+        const int vb = g == 0 ? (Q2 % 2 == 0 ? Q2 / 2 : -1) : Q2 - g;
+        cx<T> A[P2], Bc[P2];
+  #pragma unroll
+        for (int u = 0; u < P2; ++u) A[u] = ldc<T>(row + Q2 * u + va);
+        if (vb >= 0) {
+  #pragma unroll
+          for (int u = 0; u < P2; ++u) Bc[u] = ldc<T>(row + Q2 * u + vb);
         }
-        if (kk != k) {
-          const cx<T> e = cadd(b, cconj(a)), d = csub(b, cconj(a));
-          stc<T>(row + kk, cadd(e, cmul_i<+1>(cmulc(d, ldc<T>(tw + kk)))));
+        const V2* twa = tw + TL::kLinT + va * P2;
+        const V2* twb = tw + TL::kLinT + (vb >= 0 ? vb : 0) * P2;
+        // x at element k, y at its partner H - k: the pre-processed value at k
+        auto pre = [](cx<T> x, cx<T> y, cx<T> w) {
+          const cx<T> e = cadd(x, cconj(y)), d = csub(x, cconj(y));
+          return cadd(e, cmul_i<+1>(cmulc(d, w)));
+        };
+        if (g == 0) {
+          {
+            const cx<T> z = A[0];
+            A[0] = {z.re + z.im, z.re - z.im};
+          }
+  #pragma unroll
+          for (int u = 1; u <= P2 / 2; ++u) {
+            const cx<T> x = A[u], y = A[P2 - u];
+            A[u] = pre(x, y, ldc<T>(twa + u));
+            if (P2 - u != u) A[P2 - u] = pre(y, x, ldc<T>(twa + P2 - u));
+          }
+          if (vb >= 0) {
+  #pragma unroll
+            for (int u = 0; u < P2 / 2; u += 2) {
+              cx<T> w0, w1, w2, w3;
+              ld_tw2<T>(twb + u, w0, w1);
+              ld_tw2<T>(twb + P2 - 2 - u, w2, w3);
+              const cx<T> x0 = Bc[u], y0 = Bc[P2 - 1 - u], x1 = Bc[u + 1], y1 = Bc[P2 - 2 - u];
+              Bc[u] = pre(x0, y0, w0);
+              Bc[P2 - 1 - u] = pre(y0, x0, w3);
+              Bc[u + 1] = pre(x1, y1, w1);
+              Bc[P2 - 2 - u] = pre(y1, x1, w2);
+            }
+          }
+        } else {
+  #pragma unroll
+          for (int u = 0; u < P2; u += 2) {
+            cx<T> w0, w1, w2, w3;
+            ld_tw2<T>(twa + u, w0, w1);
+            ld_tw2<T>(twb + P2 - 2 - u, w2, w3);
+            const cx<T> x0 = A[u], y0 = Bc[P2 - 1 - u], x1 = A[u + 1], y1 = Bc[P2 - 2 - u];
+            A[u] = pre(x0, y0, w0);
+            Bc[P2 - 1 - u] = pre(y0, x0, w3);
+            A[u + 1] = pre(x1, y1, w1);
+            Bc[P2 - 2 - u] = pre(y1, x1, w2);
+          }
+        }
+        Dft<P2, +1, T>::run(A);
+  #pragma unroll
+        for (int p = 0; p < P2; p += 2) {
+          cx<T> w0, w1;
+          ld_tw2<T>(tw + TL::kRvp + va * P2 + p, w0, w1);
+          stc<T>(row + p * Q2 + va, p == 0 ? A[p] : cmulc(A[p], w0));
+          stc<T>(row + (p + 1) * Q2 + va, cmulc(A[p + 1], w1));
+        }
+        if (vb >= 0) {
+          Dft<P2, +1, T>::run(Bc);
+  #pragma unroll
+          for (int p = 0; p < P2; p += 2) {
+            cx<T> w0, w1;
+            ld_tw2<T>(tw + TL::kRvp + vb * P2 + p, w0, w1);
+            stc<T>(row + p * Q2 + vb, p == 0 ? Bc[p] : cmulc(Bc[p], w0));
+            stc<T>(row + (p + 1) * Q2 + vb, cmulc(Bc[p + 1], w1));
+          }
         }
       }
-    }
-    __syncthreads();
+      __syncthreads();
+    } else {
+      // Row pre-processing for the C2R z-transform through a half-length
+      // complex IDFT: Z'[k] = (X[k] + conj X[H-k]) + i W_n^{-k} (X[k] - conj X[H-k]).
+      for (int it = threadIdx.x; it < ROWS * (H / 2 + 1); it += NT) {
+        const int r = it % ROWS;
+        const int k = it / ROWS;
+        V2* row = rows + r * RS;
+        if (k == 0) {
+          const cx<T> z = ldc<T>(row);
+          stc<T>(row, cx<T>{z.re + z.im, z.re - z.im});
+        } else {
+          const int kk = H - k;
+          const cx<T> a = ldc<T>(row + k), b = ldc<T>(row + kk);
+          {
+            const cx<T> e = cadd(a, cconj(b)), d = csub(a, cconj(b));
+            stc<T>(row + k, cadd(e, cmul_i<+1>(cmulc(d, ldc<T>(tw + k)))));
+          }
+          if (kk != k) {
+            const cx<T> e = cadd(b, cconj(a)), d = csub(b, cconj(a));
+            stc<T>(row + kk, cadd(e, cmul_i<+1>(cmulc(d, ldc<T>(tw + kk)))));
+          }
+        }
+      }
+      __syncthreads();
 
-    // Row stage I1 (per v2): IDFT_P2 over u of Z'[Q2 u + v2], twiddle
-    // W_{n/2}^{-p v2} = W_n^{-2 p v2}, back to column p*Q2 + v2.
-    for (int it = threadIdx.x; it < ROWS * Q2; it += NT) {
-      const int r = it % ROWS;
-      const int v = it / ROWS;
-      V2* row = rows + r * RS;
-      cx<T> X[P2];
-#pragma unroll
-      for (int u = 0; u < P2; ++u) X[u] = ldc<T>(row + Q2 * u + v);
-      Dft<P2, +1, T>::run(X);
-      cx<T> w[P2];
-      ld_tw_row<T, P2>(tw + TL::kRvp + v * P2, w);
-#pragma unroll
-      for (int p = 0; p < P2; ++p) stc<T>(row + p * Q2 + v, p == 0 ? X[p] : cmulc(X[p], w[p]));
+      // Row stage I1 (per v2): IDFT_P2 over u of Z'[Q2 u + v2], twiddle
+      // W_{n/2}^{-p v2} = W_n^{-2 p v2}, back to column p*Q2 + v2.
+      for (int it = threadIdx.x; it < ROWS * Q2; it += NT) {
+        const int r = it % ROWS;
+        const int v = it / ROWS;
+        V2* row = rows + r * RS;
+        cx<T> X[P2];
+  #pragma unroll
+        for (int u = 0; u < P2; ++u) X[u] = ldc<T>(row + Q2 * u + v);
+        Dft<P2, +1, T>::run(X);
+        cx<T> w[P2];
+        ld_tw_row<T, P2>(tw + TL::kRvp + v * P2, w);
+  #pragma unroll
+        for (int p = 0; p < P2; ++p) stc<T>(row + p * Q2 + v, p == 0 ? X[p] : cmulc(X[p], w[p]));
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 
   // Row stage I2 + messenger draw + forward stage F1, per pair (p, p+1):
@@ -322,45 +433,124 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
   if constexpr (MODE == kModeMaterialize) return;
   __syncthreads();
 
-  // Row stage F2 (per v2): DFT_P2 over p of column p*Q2 + v2 -> Z''[Q2 u + v2].
-  for (int it = threadIdx.x; it < ROWS * Q2; it += NT) {
-    const int r = it % ROWS;
-    const int v = it / ROWS;
-    V2* row = rows + r * RS;
-    cx<T> X[P2];
-#pragma unroll
-    for (int p = 0; p < P2; ++p) X[p] = ldc<T>(row + p * Q2 + v);
-    Dft<P2, -1, T>::run(X);
-#pragma unroll
-    for (int u = 0; u < P2; ++u) stc<T>(row + Q2 * u + v, X[u]);
-  }
-  __syncthreads();
-
-  // Row post-processing of the R2C z-transform:
-  // X[k] = (Z[k] + conj Z[H-k])/2 - i W_n^{k} (Z[k] - conj Z[H-k])/2, and the
-  // real X[0], X[n/2] packed as X[0] + i X[n/2].
-  for (int it = threadIdx.x; it < ROWS * (H / 2 + 1); it += NT) {
-    const int r = it % ROWS;
-    const int k = it / ROWS;
-    V2* row = rows + r * RS;
-    if (k == 0) {
-      const cx<T> z = ldc<T>(row);
-      stc<T>(row, cx<T>{z.re + z.im, z.re - z.im});
-    } else {
-      const int kk = H - k;
-      const cx<T> a = ldc<T>(row + k), b = ldc<T>(row + kk);
-      const T h = T(0.5);
-      {
-        const cx<T> e = cscale(cadd(a, cconj(b)), h), o = cscale(csub(a, cconj(b)), h);
-        stc<T>(row + k, cadd(e, cmul(cmul_i<-1>(o), ldc<T>(tw + k))));
-      }
-      if (kk != k) {
-        const cx<T> e = cscale(cadd(b, cconj(a)), h), o = cscale(csub(b, cconj(a)), h);
-        stc<T>(row + kk, cadd(e, cmul(cmul_i<-1>(o), ldc<T>(tw + kk))));
+  if constexpr (kFuseRows) {
+    // Row stage F2 with the R2C post-processing folded in: DFT_P2 over p of
+    // column slots p*Q2 + v gives Z[k], k = Q2 u + v, and
+    //   X[k] = (Z[k] + conj Z[H-k])/2 - i W_n^{k} (Z[k] - conj Z[H-k])/2,
+    // with the real X[0], X[n/2] packed as X[0] + i X[n/2].  Items take the
+    // column pairs of row stage I1.
+    {
+      constexpr int NG = (Q2 + 1) / 2;
+      for (int it = threadIdx.x; it < ROWS * NG; it += NT) {
+        const int r = it % ROWS;
+        const int g = it / ROWS;
+        V2* row = rows + r * RS;
+        const int va = g;
+        const int vb = g == 0 ? (Q2 % 2 == 0 ? Q2 / 2 : -1) : Q2 - g;
+        cx<T> A[P2], Bc[P2];
+  #pragma unroll
+        for (int p = 0; p < P2; ++p) A[p] = ldc<T>(row + p * Q2 + va);
+        Dft<P2, -1, T>::run(A);
+        if (vb >= 0) {
+  #pragma unroll
+          for (int p = 0; p < P2; ++p) Bc[p] = ldc<T>(row + p * Q2 + vb);
+          Dft<P2, -1, T>::run(Bc);
+        }
+        const V2* twa = tw + TL::kLinT + va * P2;
+        const V2* twb = tw + TL::kLinT + (vb >= 0 ? vb : 0) * P2;
+        // x at element k, y at its partner H - k: the post-processed value at k
+        auto post = [](cx<T> x, cx<T> y, cx<T> w) {
+          const T h = T(0.5);
+          const cx<T> e = cscale(cadd(x, cconj(y)), h), o = cscale(csub(x, cconj(y)), h);
+          return cadd(e, cmul(cmul_i<-1>(o), w));
+        };
+        if (g == 0) {
+          {
+            const cx<T> z = A[0];
+            A[0] = {z.re + z.im, z.re - z.im};
+          }
+  #pragma unroll
+          for (int u = 1; u <= P2 / 2; ++u) {
+            const cx<T> x = A[u], y = A[P2 - u];
+            A[u] = post(x, y, ldc<T>(twa + u));
+            if (P2 - u != u) A[P2 - u] = post(y, x, ldc<T>(twa + P2 - u));
+          }
+          if (vb >= 0) {
+  #pragma unroll
+            for (int u = 0; u < P2 / 2; u += 2) {
+              cx<T> w0, w1, w2, w3;
+              ld_tw2<T>(twb + u, w0, w1);
+              ld_tw2<T>(twb + P2 - 2 - u, w2, w3);
+              const cx<T> x0 = Bc[u], y0 = Bc[P2 - 1 - u], x1 = Bc[u + 1], y1 = Bc[P2 - 2 - u];
+              Bc[u] = post(x0, y0, w0);
+              Bc[P2 - 1 - u] = post(y0, x0, w3);
+              Bc[u + 1] = post(x1, y1, w1);
+              Bc[P2 - 2 - u] = post(y1, x1, w2);
+            }
+          }
+        } else {
+  #pragma unroll
+          for (int u = 0; u < P2; u += 2) {
+            cx<T> w0, w1, w2, w3;
+            ld_tw2<T>(twa + u, w0, w1);
+            ld_tw2<T>(twb + P2 - 2 - u, w2, w3);
+            const cx<T> x0 = A[u], y0 = Bc[P2 - 1 - u], x1 = A[u + 1], y1 = Bc[P2 - 2 - u];
+            A[u] = post(x0, y0, w0);
+            Bc[P2 - 1 - u] = post(y0, x0, w3);
+            A[u + 1] = post(x1, y1, w1);
+            Bc[P2 - 2 - u] = post(y1, x1, w2);
+          }
+        }
+  #pragma unroll
+        for (int u = 0; u < P2; ++u) stc<T>(row + Q2 * u + va, A[u]);
+        if (vb >= 0) {
+  #pragma unroll
+          for (int u = 0; u < P2; ++u) stc<T>(row + Q2 * u + vb, Bc[u]);
+        }
       }
     }
+    __syncthreads();
+  } else {
+    // Row stage F2 (per v2): DFT_P2 over p of column p*Q2 + v2 -> Z''[Q2 u + v2].
+    for (int it = threadIdx.x; it < ROWS * Q2; it += NT) {
+      const int r = it % ROWS;
+      const int v = it / ROWS;
+      V2* row = rows + r * RS;
+      cx<T> X[P2];
+  #pragma unroll
+      for (int p = 0; p < P2; ++p) X[p] = ldc<T>(row + p * Q2 + v);
+      Dft<P2, -1, T>::run(X);
+  #pragma unroll
+      for (int u = 0; u < P2; ++u) stc<T>(row + Q2 * u + v, X[u]);
+    }
+    __syncthreads();
+
+    // Row post-processing of the R2C z-transform:
+    // X[k] = (Z[k] + conj Z[H-k])/2 - i W_n^{k} (Z[k] - conj Z[H-k])/2, and the
+    // real X[0], X[n/2] packed as X[0] + i X[n/2].
+    for (int it = threadIdx.x; it < ROWS * (H / 2 + 1); it += NT) {
+      const int r = it % ROWS;
+      const int k = it / ROWS;
+      V2* row = rows + r * RS;
+      if (k == 0) {
+        const cx<T> z = ldc<T>(row);
+        stc<T>(row, cx<T>{z.re + z.im, z.re - z.im});
+      } else {
+        const int kk = H - k;
+        const cx<T> a = ldc<T>(row + k), b = ldc<T>(row + kk);
+        const T h = T(0.5);
+        {
+          const cx<T> e = cscale(cadd(a, cconj(b)), h), o = cscale(csub(a, cconj(b)), h);
+          stc<T>(row + k, cadd(e, cmul(cmul_i<-1>(o), ldc<T>(tw + k))));
+        }
+        if (kk != k) {
+          const cx<T> e = cscale(cadd(b, cconj(a)), h), o = cscale(csub(b, cconj(a)), h);
+          stc<T>(row + kk, cadd(e, cmul(cmul_i<-1>(o), ldc<T>(tw + kk))));
+        }
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
 
   // Column stage F1 (per p of this CTA, local): DFT_Q over q of slot p*Q + q,
   // twiddle W_N^{p v}, back to slot p*Q + v.
@@ -381,10 +571,13 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
 
   // Column stage F2 (per v of this CTA): DFT_P over p of slot p*Q + v (any
   // CTA) -> X[Q u + v] -> global; the packed column 0 goes to CTA 0's scratch.
+  // A thread's last batch of items is stored to global memory after it has
+  // arrived at the final cluster barrier, so the arrive does not wait for
+  // those stores to drain (with one batch per thread, the common case, no
+  // global store precedes the arrive).
   constexpr int TF2 = H * QC;
   constexpr int BF = TF2 >= 2 * NT ? 2 : 1;
-  for (int it0 = threadIdx.x; it0 < TF2; it0 += BF * NT) {
-    cx<T> X[BF][P];
+  auto f2_transform = [&](int it0, cx<T> (&X)[BF][P]) {
 #pragma unroll
     for (int b = 0; b < BF; ++b) {
       const int it = it0 + b * NT;
@@ -403,13 +596,9 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
     for (int b = 0; b < BF; ++b) {
       const int it = it0 + b * NT;
       if (it >= TF2) continue;
-      const int l = it % H;
       const int v = int(rank) * QC + it / H;
       Dft<P, -1, T>::run(X[b]);
-      if (l != 0) {
-#pragma unroll
-        for (int u = 0; u < P; ++u) stc<T>(mainp + size_t(Q * u + v) * H + l, X[b][u]);
-      } else {
+      if (it % H == 0) {
 #pragma unroll
         for (int u = 0; u < P; ++u) {
           if constexpr (C == 1) stc<T>(col0 + Q * u + v, X[b][u]);
@@ -417,8 +606,32 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
         }
       }
     }
+  };
+  auto f2_store = [&](int it0, const cx<T> (&X)[BF][P]) {
+#pragma unroll
+    for (int b = 0; b < BF; ++b) {
+      const int it = it0 + b * NT;
+      if (it >= TF2 || it % H == 0) continue;
+      const int l = it % H;
+      const int v = int(rank) * QC + it / H;
+#pragma unroll
+      for (int u = 0; u < P; ++u) stc<T>(mainp + size_t(Q * u + v) * H + l, X[b][u]);
+    }
+  };
+  int it0 = threadIdx.x;
+  for (; it0 + BF * NT < TF2; it0 += BF * NT) {
+    cx<T> X[BF][P];
+    f2_transform(it0, X);
+    f2_store(it0, X);
   }
-  cluster_barrier<C>();
+  {
+    cx<T> X[BF][P];
+    const bool last = it0 < TF2;
+    if (last) f2_transform(it0, X);
+    cluster_arrive<C>();
+    if (last) f2_store(it0, X);
+  }
+  cluster_wait<C>();
 
   // Unpack column 0: F = A + i B with A (kz = 0) and B (kz = n/2) Hermitian in ky.
   if (rank == 0) {
