@@ -90,19 +90,31 @@ __device__ __forceinline__ void shell_accumulate(T v1, T v2, int bin, T* accw, i
   }
 }
 
-// The signal draw of one stored mode (kx, ky, kz).  F is the unnormalised
-// forward DFT of t, i.e. sqrt(M) t_hat.  With the shell's coefficients
-// (a/M, sd/sqrt(M)) the result is s_hat / sqrt(M), the value the unnormalised
-// inverse transforms turn into s.  Reports the shell id (or -1), w |s_hat|^2 / M
-// (the shell draw multiplies the sums by M) and the mode's w squared normals.
+// Shell id of stored mode (kx, ky, kz) and its coefficients (a/M, sd/sqrt(M));
+// the DC mode gets id -1 and the zero coefficients of entry B+1.  The id
+// depends on |m|^2 only, so the modes kx and n - kx share it.
 template <typename T, int N>
-__device__ __forceinline__ cx<T> draw_mode(cx<T> F, int kx, int ky, int kz, bool valid,
-                                           const ChainDev<T>& cd, uint32_t sweep, uint32_t k0, uint32_t k1,
-                                           uint32_t cid, int& bin, T& sig, T& chi) {
+__device__ __forceinline__ int mode_shell(int kx, int ky, int kz, const ChainDev<T>& cd, cx<T>& cf) {
   constexpr int H = N / 2;
   const int mx = kx <= H ? kx : kx - N;
   const int my = ky <= H ? ky : ky - N;
   const int m2 = mx * mx + my * my + kz * kz;
+  const bool dc = (m2 == 0);
+  const int bin = dc ? -1 : int(__ldg(cd.bin_of_m2 + m2));
+  cf = ldc<T>(cd.coef + (dc ? cd.B + 1 : bin));
+  return bin;
+}
+
+// The signal draw of one stored mode (kx, ky, kz) with its shell's
+// coefficients cf.  F is the unnormalised forward DFT of t, i.e.
+// sqrt(M) t_hat; with cf = (a/M, sd/sqrt(M)) the result is s_hat / sqrt(M),
+// the value the unnormalised inverse transforms turn into s.  Reports
+// w |s_hat|^2 / M (the shell draw multiplies the sums by M) and the mode's w
+// squared normals.
+template <typename T, int N>
+__device__ __forceinline__ cx<T> sample_mode(cx<T> F, cx<T> cf, int kx, int ky, int kz, uint32_t sweep,
+                                             uint32_t k0, uint32_t k1, uint32_t cid, T& sig, T& chi) {
+  constexpr int H = N / 2;
   const uint32_t j = uint32_t((kx * N + ky) * (H + 1) + kz);
   const bool edge = (kz == 0) || (kz == H);
   const u32x4 w = philox4x32_10(j, sweep, cid, kStreamModes, k0, k1);
@@ -132,12 +144,21 @@ __device__ __forceinline__ cx<T> draw_mode(cx<T> F, int kx, int ky, int kz, bool
       xi = {p0 * rs2, -(p1 * rs2)};
     }
   }
-  const bool dc = (m2 == 0);
-  bin = dc ? -1 : int(__ldg(cd.bin_of_m2 + m2));
-  const cx<T> cf = ldc<T>(cd.coef + (dc ? cd.B + 1 : bin));
   const cx<T> s = {cf.re * F.re + cf.im * xi.re, cf.re * F.im + cf.im * xi.im};
   sig = wgt * (s.re * s.re + s.im * s.im);
-  if (!valid || dc) {
+  return s;
+}
+
+// The signal draw of one stored mode, with its shell id (or -1: DC or a
+// padding lane, which then contribute nothing to the shell sums).
+template <typename T, int N>
+__device__ __forceinline__ cx<T> draw_mode(cx<T> F, int kx, int ky, int kz, bool valid,
+                                           const ChainDev<T>& cd, uint32_t sweep, uint32_t k0, uint32_t k1,
+                                           uint32_t cid, int& bin, T& sig, T& chi) {
+  cx<T> cf;
+  bin = mode_shell<T, N>(kx, ky, kz, cd, cf);
+  const cx<T> s = sample_mode<T, N>(F, cf, kx, ky, kz, sweep, k0, k1, cid, sig, chi);
+  if (!valid || bin < 0) {
     bin = -1;
     sig = T(0);
     chi = T(0);
@@ -318,43 +339,124 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
   // The modes kx = Q u + v pass through their shared-memory slots u*Q + v so
   // that the draw runs as one compact (not unrolled) loop over u.
   T* accw = acc + warp * B1 * Acc<T>::kWords;
-  for (int it = threadIdx.x; it < LW * Q; it += NT) {
-    const int vq = it / LW;
-    cx<T> X[P];
+  // Sweep tiles with an even Q and enough column pairs for every thread take
+  // the columns {v, Q-v} (item 0: {0, Q/2}) together: mode kx = Q u + v and
+  // mode n - kx = Q (P-1-u) + (Q-v) (or, in columns 0 and Q/2, the partner in
+  // the same column) are both in the thread, share one shell, and enter the
+  // shell sums as one term.
+  constexpr bool kPair = !kAdj && Q % 2 == 0 && (LW * (Q / 2)) % NT == 0;
+  if constexpr (kPair) {
+    auto f2_col = [&](int vq) {
+      cx<T> X[P];
 #pragma unroll
-    for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs + (p * Q + vq) * LW + lane);
-    Dft<P, -1, T>::run(X);
-#pragma unroll
-    for (int u = 0; u < P; ++u) stc<T>(xs + (u * Q + vq) * LW + lane, X[u]);
-    if constexpr (kAdj) {
-#pragma unroll
-      for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs2 + (p * Q + vq) * LW + lane);
+      for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs + (p * Q + vq) * LW + lane);
       Dft<P, -1, T>::run(X);
 #pragma unroll
-      for (int u = 0; u < P; ++u) stc<T>(xs2 + (u * Q + vq) * LW + lane, X[u]);
-    }
+      for (int u = 0; u < P; ++u) stc<T>(xs + (u * Q + vq) * LW + lane, X[u]);
+    };
+    auto i1_col = [&](int vq) {
+      cx<T> X[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs + (p * Q + vq) * LW + lane);
+      Dft<P, +1, T>::run(X);
+      cx<T> w[P];
+      ld_tw_row<T, P>(a.tw + TL::kCvp + vq * P, w);
+#pragma unroll
+      for (int p = 0; p < P; ++p) stc<T>(xs + (p * Q + vq) * LW + lane, p == 0 ? X[p] : cmulc(X[p], w[p]));
+    };
+    for (int it = threadIdx.x; it < LW * (Q / 2); it += NT) {
+      const int g = it / LW;  // the same for the whole warp
+      const int va = g, vb = g == 0 ? Q / 2 : Q - g;
+      f2_col(va);
+      f2_col(vb);
+      // g > 0: P pairs (u, P-1-u) across the two columns.  g == 0: the
+      // self-paired modes kx = 0 and n/2 alone, then the pairs (u, P-u) of
+      // column 0 and (u, P-1-u) of column Q/2.
+      const int steps = g == 0 ? P + 1 : P;
 #pragma unroll 1
-    for (int u = 0; u < P; ++u) {
-      V2* slot = xs + (u * Q + vq) * LW + lane;
-      int bin;
-      T sg, ch;
-      cx<T> y;
-      if constexpr (!kAdj) {
-        y = draw_mode<T, N>(ldc<T>(slot), Q * u + vq, ky, kz, valid, cd, sweep, k0, k1, cid, bin, sg, ch);
-      } else {
-        y = adjoint_mode<T, N, MODE>(ldc<T>(slot), ldc<T>(xs2 + (u * Q + vq) * LW + lane), Q * u + vq, ky, kz,
-                                     valid, cd, sweep, k0, k1, cid, bin, sg, ch);
+      for (int t = 0; t < steps; ++t) {
+        int ua, ca, ub, cb;
+        bool two = true;
+        if (g != 0) {
+          ua = t;
+          ca = va;
+          ub = P - 1 - t;
+          cb = vb;
+        } else if (t < 2) {
+          ua = t * (P / 2);
+          ca = 0;
+          ub = ua;
+          cb = 0;
+          two = false;
+        } else if (t < P / 2 + 1) {
+          ua = t - 1;
+          ca = 0;
+          ub = P - ua;
+          cb = 0;
+        } else {
+          ua = t - (P / 2 + 1);
+          ca = Q / 2;
+          ub = P - 1 - ua;
+          cb = Q / 2;
+        }
+        V2* sa = xs + (ua * Q + ca) * LW + lane;
+        V2* sb = xs + (ub * Q + cb) * LW + lane;
+        cx<T> cf;
+        int bin = mode_shell<T, N>(Q * ua + ca, ky, kz, cd, cf);
+        T sg, ch, sg2 = T(0), ch2 = T(0);
+        stc<T>(sa, sample_mode<T, N>(ldc<T>(sa), cf, Q * ua + ca, ky, kz, sweep, k0, k1, cid, sg, ch));
+        if (two) stc<T>(sb, sample_mode<T, N>(ldc<T>(sb), cf, Q * ub + cb, ky, kz, sweep, k0, k1, cid, sg2, ch2));
+        sg += sg2;
+        ch += ch2;
+        if (!valid || bin < 0) {
+          bin = -1;
+          sg = T(0);
+          ch = T(0);
+        }
+        shell_accumulate<T>(sg, ch, bin, accw, lane);
       }
-      stc<T>(slot, y);
-      shell_accumulate<T>(sg, ch, bin, accw, lane);
+      i1_col(va);
+      i1_col(vb);
     }
+  } else {
+    for (int it = threadIdx.x; it < LW * Q; it += NT) {
+      const int vq = it / LW;
+      cx<T> X[P];
 #pragma unroll
-    for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs + (p * Q + vq) * LW + lane);
-    Dft<P, +1, T>::run(X);
-    cx<T> w[P];
-    ld_tw_row<T, P>(a.tw + TL::kCvp + vq * P, w);
+      for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs + (p * Q + vq) * LW + lane);
+      Dft<P, -1, T>::run(X);
 #pragma unroll
-    for (int p = 0; p < P; ++p) stc<T>(xs + (p * Q + vq) * LW + lane, p == 0 ? X[p] : cmulc(X[p], w[p]));
+      for (int u = 0; u < P; ++u) stc<T>(xs + (u * Q + vq) * LW + lane, X[u]);
+      if constexpr (kAdj) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs2 + (p * Q + vq) * LW + lane);
+        Dft<P, -1, T>::run(X);
+#pragma unroll
+        for (int u = 0; u < P; ++u) stc<T>(xs2 + (u * Q + vq) * LW + lane, X[u]);
+      }
+#pragma unroll 1
+      for (int u = 0; u < P; ++u) {
+        V2* slot = xs + (u * Q + vq) * LW + lane;
+        int bin;
+        T sg, ch;
+        cx<T> y;
+        if constexpr (!kAdj) {
+          y = draw_mode<T, N>(ldc<T>(slot), Q * u + vq, ky, kz, valid, cd, sweep, k0, k1, cid, bin, sg, ch);
+        } else {
+          y = adjoint_mode<T, N, MODE>(ldc<T>(slot), ldc<T>(xs2 + (u * Q + vq) * LW + lane), Q * u + vq, ky, kz,
+                                       valid, cd, sweep, k0, k1, cid, bin, sg, ch);
+        }
+        stc<T>(slot, y);
+        shell_accumulate<T>(sg, ch, bin, accw, lane);
+      }
+#pragma unroll
+      for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs + (p * Q + vq) * LW + lane);
+      Dft<P, +1, T>::run(X);
+      cx<T> w[P];
+      ld_tw_row<T, P>(a.tw + TL::kCvp + vq * P, w);
+#pragma unroll
+      for (int p = 0; p < P; ++p) stc<T>(xs + (p * Q + vq) * LW + lane, p == 0 ? X[p] : cmulc(X[p], w[p]));
+    }
   }
   __syncthreads();
 
