@@ -403,11 +403,18 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
         V2* sb = xs + (ub * Q + cb) * LW + lane;
         cx<T> cf;
         int bin = mode_shell<T, N>(Q * ua + ca, ky, kz, cd, cf);
-        T sg, ch, sg2 = T(0), ch2 = T(0);
-        stc<T>(sa, sample_mode<T, N>(ldc<T>(sa), cf, Q * ua + ca, ky, kz, sweep, k0, k1, cid, sg, ch));
-        if (two) stc<T>(sb, sample_mode<T, N>(ldc<T>(sb), cf, Q * ub + cb, ky, kz, sweep, k0, k1, cid, sg2, ch2));
-        sg += sg2;
-        ch += ch2;
+        // Both draws are made unconditionally (a lone mode draws itself twice
+        // and keeps one) so that the two independent Philox and Box-Muller
+        // chains interleave.
+        T sg, ch, sg2, ch2;
+        const cx<T> ya = sample_mode<T, N>(ldc<T>(sa), cf, Q * ua + ca, ky, kz, sweep, k0, k1, cid, sg, ch);
+        const cx<T> yb = sample_mode<T, N>(ldc<T>(sb), cf, Q * ub + cb, ky, kz, sweep, k0, k1, cid, sg2, ch2);
+        stc<T>(sa, ya);
+        if (two) {
+          stc<T>(sb, yb);
+          sg += sg2;
+          ch += ch2;
+        }
         if (!valid || bin < 0) {
           bin = -1;
           sg = T(0);
