@@ -40,6 +40,12 @@ __device__ __forceinline__ void stc(typename VT<T>::c2* p, cx<T> a) {
   *p = v;
 }
 
+// sqrt(x) for x >= 0 as the messenger draw needs it: correctly rounded in
+// FP64; in FP32 x * rsqrtf(x) (a few ulp, well inside the FP32 path's error
+// budget, and several instructions cheaper than the correctly rounded root).
+__device__ __forceinline__ double msg_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float msg_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
 // Device status bits (sticky on the context once read by the host).
 enum : int { kStNumeric = 1, kStTimeout = 2, kStBadInput = 4, kStNoObserved = 8 };
 

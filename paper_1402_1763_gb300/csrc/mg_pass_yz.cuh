@@ -411,10 +411,10 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
         normal_pair<T>(w.x, w.y, g0, g1);
         normal_pair<T>(w.z, w.w, g2, g3);
         const cx<T> bc0 = bcv[0], bc1 = bcv[1], bc2 = bcv[2], bc3 = bcv[3];
-        Z0[q].re = bc0.im + bc0.re * Z0[q].re + sqrt(tau * bc0.re) * g0;
-        Z0[q].im = bc1.im + bc1.re * Z0[q].im + sqrt(tau * bc1.re) * g1;
-        Z1[q].re = bc2.im + bc2.re * Z1[q].re + sqrt(tau * bc2.re) * g2;
-        Z1[q].im = bc3.im + bc3.re * Z1[q].im + sqrt(tau * bc3.re) * g3;
+        Z0[q].re = bc0.im + bc0.re * Z0[q].re + msg_sqrt(tau * bc0.re) * g0;
+        Z0[q].im = bc1.im + bc1.re * Z0[q].im + msg_sqrt(tau * bc1.re) * g1;
+        Z1[q].re = bc2.im + bc2.re * Z1[q].re + msg_sqrt(tau * bc2.re) * g2;
+        Z1[q].im = bc3.im + bc3.re * Z1[q].im + msg_sqrt(tau * bc3.re) * g3;
       }
     }
     if constexpr (MODE != kModeMaterialize) {
