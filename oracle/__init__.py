@@ -12,6 +12,7 @@ Modules:
   sampler  tau and N~ (Sec. 2), Alg. 1, Alg. 2 on shells, the chain driver
   adjoint  torch FP64 autograd of a fixed-P chain of sweeps (differentiation workload)
 
-Parity status of each function is listed in DESIGN.md ("oracle pins").
+Every function is pinned by CPU tests (tests/test_oracle_*.py) against values
+the paper or the mathematics fixes, not against the oracle itself.
 """
 from . import philox, bins, sampler  # noqa: F401

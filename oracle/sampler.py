@@ -5,7 +5,7 @@ module; only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
 baseline use it.  It shares no code with the CUDA library: it is numpy in FP64,
 written from the paper's equations in the order the paper gives them.
 
-Conventions (the paper leaves them open; the readings are listed in the design doc):
+Conventions (where the paper leaves them open, these are the readings taken):
 
 * Grid n = (nx, ny, nz), side L = (Lx, Ly, Lz), M = nx*ny*nz voxels, V = Lx*Ly*Lz.
   Voxel index i = (ix*ny + iy)*nz + iz (z fastest).  Arrays have shape
