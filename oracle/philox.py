@@ -34,6 +34,7 @@ MASK32 = np.uint64(0xFFFFFFFF)
 
 STREAM_MESSENGER = 0
 STREAM_MODES = 1
+STREAM_MIXING = 4  # the mixing sampler's per-shell proposals (oracle/mixing.py)
 
 
 def philox4x32_10(c0, c1, c2, c3, seed: int):
