@@ -91,6 +91,15 @@ typedef struct {
                              provides (y/z cluster size per grid size, the
                              persistent launch) on the context's own chains
                              and keep the fastest (see mg_tune).  Default 0. */
+  int32_t mixing;         /* nonzero: every sweep is the messenger draw
+                             followed by the mixing sampler of Sec. 3.3
+                             (Alg. 3) on the shells instead of Alg. 1's
+                             signal draw and Alg. 2: x = s_hat/sqrt(S) drawn
+                             given S and t, then one Metropolis-Hastings
+                             update of sqrt(S_b) per shell with a truncated
+                             normal proposal (Philox stream 4), then
+                             s_hat = sqrt(S) x.  Not with persistent (gives
+                             MG_EUNSUPPORTED) or fix_P.  Default 0.          */
 } mg_options;
 
 /* Chain statistics (mg_read_stats). Arrays are caller-owned with the sizes
@@ -102,7 +111,9 @@ typedef struct {
   int32_t n_bins;         /* shells of the chain's group (excluding overflow)*/
   int64_t* n_b;           /* [n_bins+1] full-grid modes per shell (out)       */
   double* sigma_b;        /* [n_bins+1] last sweep's sum_k w_k |s_hat_k|^2    */
-  double* chi_b;          /* [n_bins+1] last sweep's chi-square draw X_b      */
+  double* chi_b;          /* [n_bins+1] last sweep's chi-square draw X_b; with
+                             mixing sweeps: 1 where the shell's proposal was
+                             accepted, else 0                                 */
   double* mean;           /* [M] per-voxel posterior mean of s (out)          */
   double* var;            /* [M] per-voxel posterior variance of s (out)      */
 } mg_stats;

@@ -27,7 +27,8 @@ class MgOptions(C.Structure):
                 ("tau_scale", C.c_double), ("P0", C.POINTER(C.c_double)),
                 ("record_every", C.c_int32), ("fix_P", C.c_int32),
                 ("timeout_cycles", C.c_int64), ("cuda_stream", C.c_void_p),
-                ("yz_cluster", C.c_int32), ("persistent", C.c_int32), ("autotune", C.c_int32)]
+                ("yz_cluster", C.c_int32), ("persistent", C.c_int32), ("autotune", C.c_int32),
+                ("mixing", C.c_int32)]
 
 
 class MgStats(C.Structure):
@@ -284,7 +285,7 @@ class Sampler:
 
     @staticmethod
     def _opts(precision, n_chains, chain_id0, tau_scale, P0, record_every, fix_P, stream,
-              yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0):
+              yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0, mixing=False):
         o = mg_options_init()
         o.precision = int(precision)
         o.n_chains = int(n_chains)
@@ -301,14 +302,15 @@ class Sampler:
         o.persistent = int(bool(persistent))
         o.autotune = int(bool(autotune))
         o.timeout_cycles = int(timeout_cycles)
+        o.mixing = int(bool(mixing))
         return o, keep
 
     @classmethod
     def single(cls, n, L, N, R, d, n_bins, seed, precision=64, n_chains=1, chain_id0=0,
                tau_scale=1.0, P0=None, record_every=0, fix_P=False, k_edges=None, stream=0,
-               yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0):
+               yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0, mixing=False):
         o, keep = cls._opts(precision, n_chains, chain_id0, tau_scale, P0, record_every, fix_P, stream,
-                            yz_cluster, persistent, autotune, timeout_cycles)
+                            yz_cluster, persistent, autotune, timeout_cycles, mixing)
         ctx = mg_init(n, L, N, R, d, n_bins, seed, o, k_edges)
         del keep
         return cls(ctx, precision)
@@ -316,9 +318,9 @@ class Sampler:
     @classmethod
     def batch(cls, ns, Ls, Ns, Rs, ds, n_bins, seeds, precision=32, n_chains=1, chain_id0=0,
               tau_scale=1.0, P0=None, record_every=0, fix_P=False, k_edges=None, stream=0,
-              yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0):
+              yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0, mixing=False):
         o, keep = cls._opts(precision, n_chains, chain_id0, tau_scale, P0, record_every, fix_P, stream,
-                            yz_cluster, persistent, autotune, timeout_cycles)
+                            yz_cluster, persistent, autotune, timeout_cycles, mixing)
         ctx = mg_init_batch(ns, Ls, Ns, Rs, ds, n_bins, seeds, o, k_edges)
         del keep
         return cls(ctx, precision)

@@ -47,7 +47,7 @@ struct Group {
 struct Chain {
   int group = 0;
   uint32_t chain_id = 0;
-  std::shared_ptr<DevBuf> main, nyq, coef, partial, P, sig, chi, mean, m2;
+  std::shared_ptr<DevBuf> main, nyq, coef, mscale, partial, P, sig, chi, mean, m2;
 };
 
 // All chains of one grid size are launched together.
@@ -66,6 +66,7 @@ struct SizeClass {
 struct mg_ctx {
   int precision = 64;
   int fix_P = 0;
+  int mixing = 0;  // sweeps use the mixing sampler (Sec. 3.3) instead of Alg. 1 + Alg. 2
   int record_every = 0;
   long long records = 0;
   cudaStream_t stream = nullptr;
@@ -236,6 +237,7 @@ mg_status upload_descriptors(mg_ctx* c) {
       d.row_info = static_cast<const uint2*>(g.row_info->p);
       d.bc_rows = static_cast<const V2*>(g.bc_rows->p);
       d.coef = static_cast<const V2*>(ch.coef->p);
+      d.mscale = static_cast<const T*>(ch.mscale->p);
       d.partial = static_cast<double*>(ch.partial->p);
       d.bin_of_m2 = static_cast<const uint8_t*>(g.bin_of_m2->p);
       d.s_out = nullptr;
@@ -282,6 +284,10 @@ mg_status upload_descriptors(mg_ctx* c) {
     d.sig_last = static_cast<double*>(ch.sig->p);
     d.chi_last = static_cast<double*>(ch.chi->p);
     d.coef = ch.coef->p;
+    d.mscale = ch.mscale->p;
+    d.k0 = uint32_t(g.seed & 0xffffffffu);
+    d.k1 = uint32_t(g.seed >> 32);
+    d.cid = ch.chain_id;
     d.tau = g.tau;
     d.M = double(g.M);
     d.V = g.L * g.L * g.L;
@@ -312,6 +318,31 @@ mg_status enqueue_passes(mg_ctx* c, int which) {
     for (auto& sc : c->classes)
       for (auto& blob : sc.args)
         MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, 0, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()), c->stream));
+  }
+  if (c->mixing) {
+    // mixing sweep: x draw and its shell sums (modes left in k space), the
+    // Metropolis-Hastings step per shell, the rescale and inverse x FFT; the
+    // sweep counter advances last
+    if (which & 2) {
+      for (auto& sc : c->classes)
+        for (auto& blob : sc.args)
+          MG_CUDA(c, launch_pass_x<T>(sc.n, kXMixDraw, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()),
+                                      sc.B_max, c->stream));
+      const dim3 grid(unsigned(c->chains.size()), unsigned(c->B_max + 1));
+      mixing_draw_kernel<T><<<grid, 256, 0, c->stream>>>(static_cast<const DrawDev*>(c->d_draw->p),
+                                                         static_cast<int*>(c->d_status->p),
+                                                         static_cast<const uint32_t*>(c->d_sweep->p));
+      MG_CUDA(c, cudaGetLastError());
+      for (auto& sc : c->classes)
+        for (auto& blob : sc.args)
+          MG_CUDA(c, launch_pass_x<T>(sc.n, kXMixScale, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()),
+                                      sc.B_max, c->stream));
+    }
+    if (which & 4) {
+      sweep_bump_kernel<<<1, 1, 0, c->stream>>>(static_cast<uint32_t*>(c->d_sweep->p));
+      MG_CUDA(c, cudaGetLastError());
+    }
+    return MG_OK;
   }
   if (which & 2) {
     for (auto& sc : c->classes)
@@ -407,7 +438,7 @@ std::string tune_key(const mg_ctx* c) {
   cudaGetDevice(&dev);
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, dev);
-  std::string k = std::string(prop.name) + "|" + std::to_string(c->precision);
+  std::string k = std::string(prop.name) + "|" + std::to_string(c->precision) + (c->mixing ? "|mix" : "");
   for (const auto& sc : c->classes) k += "|" + std::to_string(sc.n) + "x" + std::to_string(sc.chains.size());
   return k;
 }
@@ -423,7 +454,7 @@ mg_status tune_impl(mg_ctx* c, int reps) {
     if (it != g_tune_cache.end()) {
       for (size_t k = 0; k < c->classes.size(); ++k) c->classes[k].C = it->second.C[k];
       c->persist = false;
-      if (it->second.persist) {
+      if (it->second.persist && !c->mixing) {
         mg_status st = build_persist<T>(c);
         if (st != MG_OK) return st;
         c->persist = true;
@@ -506,7 +537,7 @@ mg_status tune_impl(mg_ctx* c, int reps) {
   // 2. one persistent launch per sweep against one launch per pass
   c->persist = false;
   bool use_persist = false;
-  if (persist_eligible(c)) {
+  if (!c->mixing && persist_eligible(c)) {
     if ((st = build_persist<T>(c)) != MG_OK) return st;
     float t[2];
     for (int mode = 0; mode < 2; ++mode) {
@@ -945,6 +976,9 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
       MG_CUDA(c, cudaMemsetAsync(ch.nyq->p, 0, nyq_b, c->stream));
       ch.coef = dalloc(size_t(gg.B + 2) * sizeof(V2), &e);
       MG_CUDA(c, e);
+      ch.mscale = dalloc(size_t(gg.B + 2) * sizeof(T), &e);
+      MG_CUDA(c, e);
+      MG_CUDA(c, cudaMemsetAsync(ch.mscale->p, 0, size_t(gg.B + 2) * sizeof(T), c->stream));
       ch.partial = dalloc(size_t(pass_x_tiles(gg.n)) * (gg.B + 1) * 2 * sizeof(double), &e);
       MG_CUDA(c, e);
       ch.P = dalloc(size_t(gg.B + 1) * sizeof(double), &e);
@@ -982,6 +1016,10 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
     std::memset(&none, 0, sizeof(none));  // n_chains = 0: set kernel attributes only
     for (int mode = 0; mode < 3; ++mode) MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, mode, none, c->stream));
     MG_CUDA(c, launch_pass_x<T>(sc.n, 0, none, sc.B_max, c->stream));
+    if (c->mixing) {
+      MG_CUDA(c, launch_pass_x<T>(sc.n, kXMixDraw, none, sc.B_max, c->stream));
+      MG_CUDA(c, launch_pass_x<T>(sc.n, kXMixScale, none, sc.B_max, c->stream));
+    }
   }
   s = launch_shell_draw<T>(c, 0, false);
   if (s != MG_OK) return s;
@@ -1012,6 +1050,9 @@ mg_status create(mg_ctx** out, int32_t n_groups, const mg_grid* grids, const dou
   if (!(opt.tau_scale > 0.0 && opt.tau_scale <= 1.0)) return fail(nullptr, MG_EINVAL, "tau_scale in (0, 1]");
   if (opt.record_every < 0) return fail(nullptr, MG_EINVAL, "record_every >= 0");
   if (opt.yz_cluster < 0) return fail(nullptr, MG_EINVAL, "yz_cluster >= 0");
+  if (opt.mixing && opt.fix_P) return fail(nullptr, MG_EINVAL, "mixing sweeps draw P; fix_P must be 0");
+  if (opt.mixing && opt.persistent)
+    return fail(nullptr, MG_EUNSUPPORTED, "mixing sweeps run one launch per pass (persistent must be 0)");
   for (int g = 0; g < n_groups; ++g) {
     mg_status s = validate_grid(&grids[g]);
     if (s != MG_OK) return fail(nullptr, s, "grid must be cubic with equal sides and n in {8,12,16,24,32,48,64,96,128,192,256}");
@@ -1028,6 +1069,7 @@ mg_status create(mg_ctx** out, int32_t n_groups, const mg_grid* grids, const dou
   auto* c = new mg_ctx();
   c->precision = opt.precision;
   c->fix_P = opt.fix_P ? 1 : 0;
+  c->mixing = opt.mixing ? 1 : 0;
   c->record_every = opt.record_every;
   c->timeout = opt.timeout_cycles > 0 ? opt.timeout_cycles : 4000000000ll;
   if (opt.cuda_stream) {
@@ -1098,6 +1140,7 @@ void mg_options_init(mg_options* o) {
   o->yz_cluster = 0;
   o->persistent = 0;
   o->autotune = 0;
+  o->mixing = 0;
 }
 
 mg_status mg_init(mg_ctx** out, const mg_grid* grid, const double* N, const double* R, const double* d,

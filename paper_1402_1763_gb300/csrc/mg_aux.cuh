@@ -195,6 +195,117 @@ __global__ void shell_draw_kernel(const DrawDev* __restrict__ chains, int draw, 
   if (sweep_ctr && blockIdx.x == 0 && b == 0) atomicAdd(sweep_ctr, 1u);
 }
 
+// A draw from N(mu, sigma^2) restricted to (0, inf) from shell b's Philox
+// calls (b + 256 k, sweep, chain, 4), k < 64: plain rejection of the first
+// Box-Muller normal of words (w0, w1) when a = -mu/sigma <= 1/2, else Robert's
+// (1995) exponential rejection with rate (a + sqrt(a^2 + 4))/2, U(w0) for the
+// exponential and U(w1) for the test.  Returns false if no attempt succeeds.
+__device__ inline bool truncated_normal_positive(double mu, double sigma, uint32_t b, uint32_t sweep,
+                                                 uint32_t cid, uint32_t k0, uint32_t k1, double* out) {
+  const double a = -mu / sigma;
+  const double lam = 0.5 * (a + sqrt(a * a + 4.0));
+  for (uint32_t k = 0; k < 64; ++k) {
+    const u32x4 w = philox4x32_10(b + 256u * k, sweep, cid, kStreamMixing, k0, k1);
+    double z;
+    if (a <= 0.5) {
+      double z1;
+      box_muller(w.x, w.y, z, z1);
+      if (!(z > a)) continue;
+    } else {
+      const double u0 = (2.0 * double(w.x) + 1.0) * 0x1p-33;
+      const double u1 = (2.0 * double(w.y) + 1.0) * 0x1p-33;
+      z = a - log(u0) / lam;
+      const double dz = z - lam;
+      if (!(u1 <= exp(-0.5 * dz * dz))) continue;
+    }
+    *out = mu + sigma * z;
+    return true;
+  }
+  return false;
+}
+
+// Mixing sweep, shell step (Sec. 3.3, Alg. 3 on k-shells).  One CTA per
+// (chain, shell).  Pass X left per tile, per shell, the sums of w |y|^2 and
+// w Re(conj(y) F) with y = a t_hat/sqrt(M) + sd xi/sqrt(M) (the plain draw
+// scaled by 1/sqrt(M)) and F = sqrt(M) t_hat; with x = y sqrt(M/S) they give
+//   B = sum w |x|^2 = (M/S) sum w |y|^2,   A = sum w Re(conj(x) t_hat) = sum w Re(conj(y) F) / sqrt(S).
+// u = sqrt(S_b) then takes one Metropolis-Hastings step: proposal
+// u' ~ N(A/B, tau/B) truncated to u' > 0, accepted with probability
+// min(1, u/u') (the conditional of u is proportional to
+// u^-1 exp(-B (u - A/B)^2 / (2 tau))), the acceptance uniform being U(w3) of
+// attempt 0.  Writes P, sigma_b = S_new B, the acceptance flag, the scale
+// sqrt(S_new/S_old) that turns y into s_hat_new / sqrt(M) in pass X, and the
+// next sweep's coefficients.  The sweep counter is read, not advanced (the
+// sweep's last kernel advances it).
+template <typename T>
+__global__ void mixing_draw_kernel(const DrawDev* __restrict__ chains, int* status, const uint32_t* sweep_ctr) {
+  const DrawDev cd = chains[blockIdx.x];
+  const int b = blockIdx.y;
+  if (b > cd.B) return;
+  const int B1 = cd.B + 1;
+  __shared__ double r1[256], r2[256];
+  double s1 = 0.0, s2 = 0.0;
+  for (int t = threadIdx.x; t < cd.n_tiles; t += blockDim.x) {
+    s1 += cd.partial[(size_t(t) * B1 + b) * 2 + 0];
+    s2 += cd.partial[(size_t(t) * B1 + b) * 2 + 1];
+  }
+  r1[threadIdx.x] = s1;
+  r2[threadIdx.x] = s2;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      r1[threadIdx.x] += r1[threadIdx.x + w];
+      r2[threadIdx.x] += r2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const uint32_t sweep = *sweep_ctr;
+  const double S_old = (cd.M / cd.V) * cd.P[b];
+  double S_new = S_old;
+  double Bx = 0.0;
+  int acc = 0;
+  if (cd.n_b[b] > 0) {
+    Bx = r1[0] * cd.M / S_old;
+    const double Ax = r2[0] / sqrt(S_old);
+    if (Bx > 0.0 && isfinite(Ax) && isfinite(Bx)) {
+      double up;
+      if (truncated_normal_positive(Ax / Bx, sqrt(cd.tau / Bx), uint32_t(b), sweep, cd.cid, cd.k0, cd.k1, &up)) {
+        const u32x4 w0 = philox4x32_10(uint32_t(b), sweep, cd.cid, kStreamMixing, cd.k0, cd.k1);
+        const double alpha = (2.0 * double(w0.w) + 1.0) * 0x1p-33;
+        if (alpha * up < sqrt(S_old)) {
+          S_new = up * up;
+          acc = 1;
+        }
+      }
+    } else {
+      atomicOr(status, kStNumeric);
+    }
+  }
+  const double P = (cd.V / cd.M) * S_new;
+  cd.P[b] = P;
+  cd.sig_last[b] = S_new * Bx;
+  cd.chi_last[b] = double(acc);
+  T* ms = static_cast<T*>(cd.mscale);
+  ms[b] = T(sqrt(S_new / S_old));
+  const double a = S_new / (S_new + cd.tau);
+  const double sd = sqrt(S_new * cd.tau / (S_new + cd.tau));
+  typename VT<T>::c2* coef = static_cast<typename VT<T>::c2*>(cd.coef);
+  typename VT<T>::c2 v;
+  v.x = T(a / cd.M);
+  v.y = T(sd / sqrt(cd.M));
+  coef[b] = v;
+  if (b == 0) {
+    ms[cd.B + 1] = T(0);
+    v.x = T(0);
+    v.y = T(0);
+    coef[cd.B + 1] = v;
+  }
+}
+
+// Advance the device sweep counter (end of a mixing sweep).
+__global__ void sweep_bump_kernel(uint32_t* sweep_ctr) { atomicAdd(sweep_ctr, 1u); }
+
 // Welford update of the per-voxel mean and sum of squared deviations of s.
 template <typename T>
 __global__ void welford_kernel(const T* __restrict__ s, double* __restrict__ mean, double* __restrict__ m2,

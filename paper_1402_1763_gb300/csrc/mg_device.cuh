@@ -69,6 +69,7 @@ struct ChainDev {
   const uint2* row_info;
   const typename VT<T>::c2* bc_rows;
   const typename VT<T>::c2* coef;  // [B+2]: (a / M, sd / sqrt(M)) per shell; [B+1] = DC
+  const T* mscale;                 // [B+2] mixing sweeps: sqrt(S_new / S_old) per shell; [B+1] = DC
   double* partial;                 // [tiles][B+1][2]: per-tile (sigma_b, X_b)
   const uint8_t* bin_of_m2;
   T* s_out;                        // real-space output of the materialise pass
@@ -160,10 +161,12 @@ struct DrawDev {
   double* P;
   double* sig_last;
   double* chi_last;
-  void* coef;  // float2 or double2 [B+2]
+  void* coef;    // float2 or double2 [B+2]
+  void* mscale;  // float or double [B+2] (mixing sweeps)
   double tau;
   double M;
   double V;
+  uint32_t k0, k1, cid;  // Philox key and chain id (mixing sweeps' proposals)
 };
 
 }  // namespace mg

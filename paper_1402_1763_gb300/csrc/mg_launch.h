@@ -21,7 +21,16 @@ template <typename T>
 cudaError_t launch_pass_yz(int n, int C, int mode, const LaunchArgs<T>& args, cudaStream_t st);
 
 int pass_x_tiles(int n);
-// mode: 0 = sweep, 1 = adjoint of the last sweep, 2 = adjoint of an earlier sweep
+
+enum PassXMode : int {
+  kXSweep = 0,     // forward x FFT, signal draw, shell sums, inverse x FFT
+  kXAdjTop = 1,    // adjoint of the last sweep: loss from the final state, gradient terms
+  kXAdjMid = 2,    // adjoint of an earlier sweep
+  kXMixDraw = 3,   // mixing sweep: forward x FFT, draw y = x sqrt(S/M), the sums of
+                   // w |y|^2 and w Re(conj(y) F); the modes stay in k space
+  kXMixScale = 4,  // mixing sweep: scale each mode by sqrt(S_new/S_old) of its shell,
+                   // inverse x FFT
+};
 template <typename T>
 cudaError_t launch_pass_x(int n, int mode, const LaunchArgs<T>& args, int B_max, cudaStream_t st);
 

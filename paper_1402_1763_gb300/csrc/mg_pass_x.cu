@@ -22,8 +22,9 @@ cudaError_t run_x(const LaunchArgs<T>& args, int B_max, cudaStream_t st) {
   const int n_chains = args.n_chains;
   constexpr int NT = pass_x_threads<N>();
   using S = PassXShape<T, N>;
-  const size_t smem = S::smem_bytes(NT / 32, B_max, MODE != kXSweep);
-  auto kern = pass_x_kernel<T, N, NT, MODE == kXSweep ? pass_x_minblocks<T, N>() : 1, MODE>;
+  constexpr bool adj = MODE == kXAdjTop || MODE == kXAdjMid;
+  const size_t smem = S::smem_bytes(NT / 32, B_max, adj);
+  auto kern = pass_x_kernel<T, N, NT, adj ? 1 : pass_x_minblocks<T, N>(), MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess || n_chains == 0) return e;  // n_chains == 0: set attributes only
   const unsigned grid = unsigned(S::kTiles) * unsigned(n_chains);
@@ -46,6 +47,10 @@ cudaError_t run_x_mode(int mode, const LaunchArgs<T>& args, int B_max, cudaStrea
       return run_x<T, N, kXAdjTop>(args, B_max, st);
     case kXAdjMid:
       return run_x<T, N, kXAdjMid>(args, B_max, st);
+    case kXMixDraw:
+      return run_x<T, N, kXMixDraw>(args, B_max, st);
+    case kXMixScale:
+      return run_x<T, N, kXMixScale>(args, B_max, st);
     default:
       return cudaErrorInvalidValue;
   }

@@ -15,6 +15,7 @@
 // shell ids along a warp come in runs, reduced with a segmented warp scan.
 #pragma once
 #include "mg_device.cuh"
+#include "mg_launch.h"
 
 namespace mg {
 
@@ -94,14 +95,17 @@ __device__ __forceinline__ void shell_accumulate(T v1, T v2, int bin, T* accw, i
 // the DC mode gets id -1 and the zero coefficients of entry B+1.  The id
 // depends on |m|^2 only, so the modes kx and n - kx share it.
 template <typename T, int N>
-__device__ __forceinline__ int mode_shell(int kx, int ky, int kz, const ChainDev<T>& cd, cx<T>& cf) {
+__device__ __forceinline__ int mode_bin(int kx, int ky, int kz, const ChainDev<T>& cd) {
   constexpr int H = N / 2;
   const int mx = kx <= H ? kx : kx - N;
   const int my = ky <= H ? ky : ky - N;
   const int m2 = mx * mx + my * my + kz * kz;
-  const bool dc = (m2 == 0);
-  const int bin = dc ? -1 : int(__ldg(cd.bin_of_m2 + m2));
-  cf = ldc<T>(cd.coef + (dc ? cd.B + 1 : bin));
+  return m2 == 0 ? -1 : int(__ldg(cd.bin_of_m2 + m2));
+}
+template <typename T, int N>
+__device__ __forceinline__ int mode_shell(int kx, int ky, int kz, const ChainDev<T>& cd, cx<T>& cf) {
+  const int bin = mode_bin<T, N>(kx, ky, kz, cd);
+  cf = ldc<T>(cd.coef + (bin < 0 ? cd.B + 1 : bin));
   return bin;
 }
 
@@ -111,7 +115,7 @@ __device__ __forceinline__ int mode_shell(int kx, int ky, int kz, const ChainDev
 // the value the unnormalised inverse transforms turn into s.  Reports
 // w |s_hat|^2 / M (the shell draw multiplies the sums by M) and the mode's w
 // squared normals.
-template <typename T, int N>
+template <typename T, int N, bool kChi = true>
 __device__ __forceinline__ cx<T> sample_mode(cx<T> F, cx<T> cf, int kx, int ky, int kz, uint32_t sweep,
                                              uint32_t k0, uint32_t k1, uint32_t cid, T& sig, T& chi) {
   constexpr int H = N / 2;
@@ -123,14 +127,17 @@ __device__ __forceinline__ cx<T> sample_mode(cx<T> F, cx<T> cf, int kx, int ky, 
   const T rs2 = T(0.70710678118654752440);
   cx<T> xi;
   T wgt;
+  chi = T(0);
   if (!edge) {
     xi = {z0 * rs2, z1 * rs2};
-    chi = radius2<T>(w.z);  // z2^2 + z3^2 of the pair (w.z, w.w)
+    if constexpr (kChi) chi = radius2<T>(w.z);  // z2^2 + z3^2 of the pair (w.z, w.w)
     wgt = T(2);
   } else {
-    T z2, z3;
-    normal_pair<T>(w.z, w.w, z2, z3);
-    chi = z2 * z2;
+    if constexpr (kChi) {
+      T z2, z3;
+      normal_pair<T>(w.z, w.w, z2, z3);
+      chi = z2 * z2;
+    }
     wgt = T(1);
     const uint32_t jp = uint32_t(((((N - kx) % N) * N) + ((N - ky) % N)) * (H + 1) + kz);
     if (jp == j) {
@@ -200,12 +207,6 @@ __device__ __forceinline__ cx<T> adjoint_mode(cx<T> G, cx<T> Ft, int kx, int ky,
                                               const ChainDev<T>& cd, uint32_t sweep, uint32_t k0, uint32_t k1,
                                               uint32_t cid, int& bin, T& grad, T& loss);
 
-enum PassXMode : int {
-  kXSweep = 0,   // forward x FFT, signal draw, shell sums, inverse x FFT
-  kXAdjTop = 1,  // adjoint of the last sweep: loss from the final state, gradient terms
-  kXAdjMid = 2,  // adjoint of an earlier sweep
-};
-
 // Adjoint of the signal draw of one mode (fixed P).  In mode kXAdjTop, G is
 // the unnormalised x transform of the final state, i.e. n s_hat / sqrt(M); the
 // loss term is w_l |s_hat|^2 and the adjoint seed G = sqrt(M) mu with
@@ -272,7 +273,8 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
   using TL = TwLayout<N>;
   constexpr int H = S::H, P = S::P, Q = S::Q, LW = S::LW;
   constexpr int NW = NT / 32;
-  constexpr bool kAdj = MODE != kXSweep;
+  constexpr bool kAdj = MODE == kXAdjTop || MODE == kXAdjMid;
+  constexpr bool kMixDraw = MODE == kXMixDraw, kMixScale = MODE == kXMixScale;
   static_assert(NT % 32 == 0, "whole warps");
   V2* xs = reinterpret_cast<V2*>(smem_raw);  // [N][LW], slot p*Q + v
   V2* xs2 = reinterpret_cast<V2*>(smem_raw + S::kXchgBytes);  // adjoint: second input
@@ -316,8 +318,15 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
     base2 = (nyq_tile ? cd.nyq2 : cd.main2) + off;
   }
 
+  // Mixing sweep, second half: the modes (kx = slot index) come back from k
+  // space; the column loop below scales them and runs the inverse stage I1.
+  if constexpr (kMixScale) {
+    for (int kx = warp; kx < N; kx += NW)
+      stc<T>(xs + kx * LW + lane, valid ? ldcg<T>(base + size_t(kx) * stride) : cx<T>{T(0), T(0)});
+  }
+
   // Stage F1: DFT_Q over q of x[p + P q], twiddle W_N^{p v}, to slot p*Q + v.
-  for (int it = threadIdx.x; it < LW * P; it += NT) {
+  for (int it = threadIdx.x; it < (kMixScale ? 0 : LW * P); it += NT) {
     const int p = it / LW;
     cx<T> w[Q];
     ld_tw_row<T, Q>(a.tw + TL::kCpv + p * Q, w);
@@ -344,8 +353,27 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
   // mode n - kx = Q (P-1-u) + (Q-v) (or, in columns 0 and Q/2, the partner in
   // the same column) are both in the thread, share one shell, and enter the
   // shell sums as one term.
-  constexpr bool kPair = !kAdj && Q % 2 == 0 && (LW * (Q / 2)) % NT == 0;
-  if constexpr (kPair) {
+  // Mixing draws accumulate (w |y|^2, w Re(conj(y) F)) instead of the
+  // signal power and the chi-square draws, and leave the modes in k space.
+  constexpr bool kPair = !kAdj && !kMixScale && Q % 2 == 0 && (LW * (Q / 2)) % NT == 0;
+  if constexpr (kMixScale) {
+    // s_hat_new / sqrt(M) = y sqrt(S_new / S_old) per shell, then I1.
+    for (int it = threadIdx.x; it < LW * Q; it += NT) {
+      const int vq = it / LW;
+      cx<T> X[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const int bin = mode_bin<T, N>(Q * p + vq, ky, kz, cd);
+        const T r = cd.mscale[bin < 0 ? cd.B + 1 : bin];
+        X[p] = cscale(ldc<T>(xs + (p * Q + vq) * LW + lane), r);
+      }
+      Dft<P, +1, T>::run(X);
+      cx<T> w[P];
+      ld_tw_row<T, P>(a.tw + TL::kCvp + vq * P, w);
+#pragma unroll
+      for (int p = 0; p < P; ++p) stc<T>(xs + (p * Q + vq) * LW + lane, p == 0 ? X[p] : cmulc(X[p], w[p]));
+    }
+  } else if constexpr (kPair) {
     auto f2_col = [&](int vq) {
       cx<T> X[P];
 #pragma unroll
@@ -407,8 +435,14 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
         // and keeps one) so that the two independent Philox and Box-Muller
         // chains interleave.
         T sg, ch, sg2, ch2;
-        const cx<T> ya = sample_mode<T, N>(ldc<T>(sa), cf, Q * ua + ca, ky, kz, sweep, k0, k1, cid, sg, ch);
-        const cx<T> yb = sample_mode<T, N>(ldc<T>(sb), cf, Q * ub + cb, ky, kz, sweep, k0, k1, cid, sg2, ch2);
+        const cx<T> Fa = ldc<T>(sa), Fb = ldc<T>(sb);
+        const cx<T> ya = sample_mode<T, N, !kMixDraw>(Fa, cf, Q * ua + ca, ky, kz, sweep, k0, k1, cid, sg, ch);
+        const cx<T> yb = sample_mode<T, N, !kMixDraw>(Fb, cf, Q * ub + cb, ky, kz, sweep, k0, k1, cid, sg2, ch2);
+        if constexpr (kMixDraw) {
+          const T wgt = (kz == 0 || kz == H) ? T(1) : T(2);
+          ch = wgt * (ya.re * Fa.re + ya.im * Fa.im);
+          ch2 = wgt * (yb.re * Fb.re + yb.im * Fb.im);
+        }
         stc<T>(sa, ya);
         if (two) {
           stc<T>(sb, yb);
@@ -422,8 +456,10 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
         }
         shell_accumulate<T>(sg, ch, bin, accw, lane);
       }
-      i1_col(va);
-      i1_col(vb);
+      if constexpr (!kMixDraw) {
+        i1_col(va);
+        i1_col(vb);
+      }
     }
   } else {
     for (int it = threadIdx.x; it < LW * Q; it += NT) {
@@ -447,7 +483,18 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
         int bin;
         T sg, ch;
         cx<T> y;
-        if constexpr (!kAdj) {
+        if constexpr (kMixDraw) {
+          const cx<T> F = ldc<T>(slot);
+          cx<T> cf;
+          bin = mode_shell<T, N>(Q * u + vq, ky, kz, cd, cf);
+          y = sample_mode<T, N, false>(F, cf, Q * u + vq, ky, kz, sweep, k0, k1, cid, sg, ch);
+          ch = ((kz == 0 || kz == H) ? T(1) : T(2)) * (y.re * F.re + y.im * F.im);
+          if (!valid || bin < 0) {
+            bin = -1;
+            sg = T(0);
+            ch = T(0);
+          }
+        } else if constexpr (!kAdj) {
           y = draw_mode<T, N>(ldc<T>(slot), Q * u + vq, ky, kz, valid, cd, sweep, k0, k1, cid, bin, sg, ch);
         } else {
           y = adjoint_mode<T, N, MODE>(ldc<T>(slot), ldc<T>(xs2 + (u * Q + vq) * LW + lane), Q * u + vq, ky, kz,
@@ -456,20 +503,28 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
         stc<T>(slot, y);
         shell_accumulate<T>(sg, ch, bin, accw, lane);
       }
+      if constexpr (!kMixDraw) {
 #pragma unroll
-      for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs + (p * Q + vq) * LW + lane);
-      Dft<P, +1, T>::run(X);
-      cx<T> w[P];
-      ld_tw_row<T, P>(a.tw + TL::kCvp + vq * P, w);
+        for (int p = 0; p < P; ++p) X[p] = ldc<T>(xs + (p * Q + vq) * LW + lane);
+        Dft<P, +1, T>::run(X);
+        cx<T> w[P];
+        ld_tw_row<T, P>(a.tw + TL::kCvp + vq * P, w);
 #pragma unroll
-      for (int p = 0; p < P; ++p) stc<T>(xs + (p * Q + vq) * LW + lane, p == 0 ? X[p] : cmulc(X[p], w[p]));
+        for (int p = 0; p < P; ++p) stc<T>(xs + (p * Q + vq) * LW + lane, p == 0 ? X[p] : cmulc(X[p], w[p]));
+      }
     }
   }
   __syncthreads();
 
+  // Mixing sweep, first half: the drawn modes go to k space (kx = slot index).
+  if constexpr (kMixDraw) {
+    if (valid)
+      for (int kx = warp; kx < N; kx += NW) stc<T>(base + size_t(kx) * stride, ldc<T>(xs + kx * LW + lane));
+  }
+
   // Stage I2: IDFT_Q over v of slot p*Q + v, out to x = p + P q (adjoint
   // passes write the adjoint state, held in main/nyq).
-  for (int it = threadIdx.x; it < LW * P; it += NT) {
+  for (int it = threadIdx.x; it < (kMixDraw ? 0 : LW * P); it += NT) {
     const int p = it / LW;
     cx<T> v[Q];
 #pragma unroll
@@ -483,7 +538,7 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
 
   // Per-tile shell sums: combine the warps in a fixed order, then FP64.
   double* part = cd.partial + size_t(tile) * B1 * 2;
-  for (int b = threadIdx.x; b < B1; b += NT) {
+  for (int b = threadIdx.x; b < (kMixScale ? 0 : B1); b += NT) {
     if constexpr (sizeof(T) == 4) {
       float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
       for (int w2 = 0; w2 < NW; ++w2) {

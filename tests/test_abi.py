@@ -44,6 +44,37 @@ def test_options_defaults_without_gpu(lib):
     from paper_1402_1763_gb300 import mg_options_init
     o = mg_options_init()
     assert o.precision == 64 and o.n_chains == 1 and o.tau_scale == 1.0 and not o.P0
+    assert o.persistent == 0 and o.autotune == 0 and o.mixing == 0
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Field offsets and sizes of the ctypes mirrors equal the C compiler's
+    layout of the structs in include/mg.h."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1402_1763_gb300._native import MgGrid, MgOptions, MgStats
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"mg_grid": MgGrid, "mg_options": MgOptions, "mg_stats": MgStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{os.path.join(ROOT, "include", "mg.h")}"',
+             "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
 
 
 def test_null_arguments_are_rejected_without_gpu(lib):
