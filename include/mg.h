@@ -91,15 +91,18 @@ typedef struct {
                              provides (y/z cluster size per grid size, the
                              persistent launch) on the context's own chains
                              and keep the fastest (see mg_tune).  Default 0. */
-  int32_t mixing;         /* nonzero: every sweep is the messenger draw
-                             followed by the mixing sampler of Sec. 3.3
-                             (Alg. 3) on the shells instead of Alg. 1's
-                             signal draw and Alg. 2: x = s_hat/sqrt(S) drawn
-                             given S and t, then one Metropolis-Hastings
-                             update of sqrt(S_b) per shell with a truncated
-                             normal proposal (Philox stream 4), then
-                             s_hat = sqrt(S) x.  Not with persistent (gives
-                             MG_EUNSUPPORTED) or fix_P.  Default 0.          */
+  int32_t mixing;         /* 1: every sweep is the messenger draw followed
+                             by the mixing sampler of Sec. 3.3 (Alg. 3) on
+                             the shells instead of Alg. 1's signal draw and
+                             Alg. 2: x = s_hat/sqrt(S) drawn given S and t,
+                             then one Metropolis-Hastings update of sqrt(S_b)
+                             per shell with a truncated normal proposal
+                             (Philox stream 4), then s_hat = sqrt(S) x.
+                             2: sweeps alternate, those with an odd sweep
+                             count (the Philox counter word 1) mixing, the
+                             others plain.  0: plain sweeps.  Not with
+                             persistent (MG_EUNSUPPORTED) or fix_P
+                             (MG_EINVAL).  Default 0.                        */
 } mg_options;
 
 /* Chain statistics (mg_read_stats). Arrays are caller-owned with the sizes

@@ -167,3 +167,20 @@ class MixingChains(sp.Chains):
                 self.prob, self.s, self.P, g, z0, z1, self.seed, self.sweeps_done, self.chain_ids)
             self.sweeps_done += 1
         return self
+
+
+class AlternatingChains(sp.Chains):
+    """Chains whose sweeps alternate: a sweep with an even sweep count is a
+    plain sweep (Alg. 1 + Alg. 2), one with an odd count a mixing sweep."""
+
+    def sweep(self, n: int = 1):
+        for _ in range(n):
+            g, z0, z1, z2, z3 = sp.sweep_draws(self.prob.shape, self.seed, self.sweeps_done, self.chain_ids)
+            if self.sweeps_done % 2 == 0:
+                self.s, self.P, _, self.last_sig, self.last_X = sp.gibbs_sweep(
+                    self.prob, self.s, self.P, g, z0, z1, z2, z3)
+            else:
+                self.s, self.P, _, self.last_sig, self.last_X = mixing_sweep(
+                    self.prob, self.s, self.P, g, z0, z1, self.seed, self.sweeps_done, self.chain_ids)
+            self.sweeps_done += 1
+        return self

@@ -302,7 +302,7 @@ class Sampler:
         o.persistent = int(bool(persistent))
         o.autotune = int(bool(autotune))
         o.timeout_cycles = int(timeout_cycles)
-        o.mixing = int(bool(mixing))
+        o.mixing = int(mixing)  # False/True, or 2 to alternate plain and mixing sweeps
         return o, keep
 
     @classmethod

@@ -66,7 +66,7 @@ struct SizeClass {
 struct mg_ctx {
   int precision = 64;
   int fix_P = 0;
-  int mixing = 0;  // sweeps use the mixing sampler (Sec. 3.3) instead of Alg. 1 + Alg. 2
+  int mixing = 0;  // 1: every sweep uses the mixing sampler (Sec. 3.3); 2: odd sweeps do
   int record_every = 0;
   long long records = 0;
   cudaStream_t stream = nullptr;
@@ -80,7 +80,8 @@ struct mg_ctx {
   long long sweeps = 0;
   mg_status sticky = MG_OK;
   std::string err;
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;      // one plain sweep
+  cudaGraphExec_t graph_mix = nullptr;  // one mixing sweep
   bool graph_failed = false;
   // persistent one-launch sweep
   bool persist = false;
@@ -311,7 +312,7 @@ mg_status launch_shell_draw(mg_ctx* c, int draw, bool count_sweep) {
 
 // which: bit 1 = pass YZ of every size class, bit 2 = pass X, bit 4 = shell draw.
 template <typename T>
-mg_status enqueue_passes(mg_ctx* c, int which) {
+mg_status enqueue_passes(mg_ctx* c, int which, bool mix) {
   const uint32_t* sw = static_cast<const uint32_t*>(c->d_sweep->p);
   (void)sw;
   if (which & 1) {
@@ -319,7 +320,7 @@ mg_status enqueue_passes(mg_ctx* c, int which) {
       for (auto& blob : sc.args)
         MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, 0, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()), c->stream));
   }
-  if (c->mixing) {
+  if (mix) {
     // mixing sweep: x draw and its shell sums (modes left in k space), the
     // Metropolis-Hastings step per shell, the rescale and inverse x FFT; the
     // sweep counter advances last
@@ -408,14 +409,20 @@ mg_status enqueue_persistent(mg_ctx* c) {
   return MG_OK;
 }
 
-mg_status enqueue_sweep(mg_ctx* c) {
+// Whether the context's next sweep is a mixing sweep (the sweep count is the
+// Philox counter word of that sweep).
+bool mixing_sweep_next(const mg_ctx* c) { return c->mixing == 1 || (c->mixing == 2 && (c->sweeps & 1)); }
+
+mg_status enqueue_sweep(mg_ctx* c, bool mix) {
   if (c->persist) return c->precision == 32 ? enqueue_persistent<float>(c) : enqueue_persistent<double>(c);
-  return c->precision == 32 ? enqueue_passes<float>(c, 7) : enqueue_passes<double>(c, 7);
+  return c->precision == 32 ? enqueue_passes<float>(c, 7, mix) : enqueue_passes<double>(c, 7, mix);
 }
 
 void drop_graph(mg_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph_mix) cudaGraphExecDestroy(c->graph_mix);
   c->graph = nullptr;
+  c->graph_mix = nullptr;
   c->graph_failed = false;
 }
 
@@ -542,10 +549,10 @@ mg_status tune_impl(mg_ctx* c, int reps) {
     float t[2];
     for (int mode = 0; mode < 2; ++mode) {
       c->persist = mode == 1;
-      if ((st = enqueue_sweep(c)) != MG_OK) return st;  // warm-up
+      if ((st = enqueue_sweep(c, false)) != MG_OK) return st;  // warm-up
       MG_CUDA(c, cudaEventRecord(e0, s));
       for (int r = 0; r < reps; ++r)
-        if ((st = enqueue_sweep(c)) != MG_OK) return st;
+        if ((st = enqueue_sweep(c, false)) != MG_OK) return st;
       MG_CUDA(c, cudaEventRecord(e1, s));
       if ((st = elapsed(&t[mode])) != MG_OK) return st;
       if ((st = restore()) != MG_OK) return st;
@@ -1050,6 +1057,7 @@ mg_status create(mg_ctx** out, int32_t n_groups, const mg_grid* grids, const dou
   if (!(opt.tau_scale > 0.0 && opt.tau_scale <= 1.0)) return fail(nullptr, MG_EINVAL, "tau_scale in (0, 1]");
   if (opt.record_every < 0) return fail(nullptr, MG_EINVAL, "record_every >= 0");
   if (opt.yz_cluster < 0) return fail(nullptr, MG_EINVAL, "yz_cluster >= 0");
+  if (opt.mixing < 0 || opt.mixing > 2) return fail(nullptr, MG_EINVAL, "mixing must be 0, 1 or 2");
   if (opt.mixing && opt.fix_P) return fail(nullptr, MG_EINVAL, "mixing sweeps draw P; fix_P must be 0");
   if (opt.mixing && opt.persistent)
     return fail(nullptr, MG_EUNSUPPORTED, "mixing sweeps run one launch per pass (persistent must be 0)");
@@ -1069,7 +1077,7 @@ mg_status create(mg_ctx** out, int32_t n_groups, const mg_grid* grids, const dou
   auto* c = new mg_ctx();
   c->precision = opt.precision;
   c->fix_P = opt.fix_P ? 1 : 0;
-  c->mixing = opt.mixing ? 1 : 0;
+  c->mixing = opt.mixing;
   c->record_every = opt.record_every;
   c->timeout = opt.timeout_cycles > 0 ? opt.timeout_cycles : 4000000000ll;
   if (opt.cuda_stream) {
@@ -1164,14 +1172,16 @@ mg_status mg_sweep(mg_ctx* c, int64_t n) {
   if (n < 0) return fail(c, MG_EINVAL, "n_sweeps must be >= 0");
   for (int64_t i = 0; i < n; ++i) {
     mg_status s = MG_OK;
-    if (!c->graph && !c->graph_failed) {
+    const bool mix = mixing_sweep_next(c);
+    cudaGraphExec_t& graph = mix ? c->graph_mix : c->graph;
+    if (!graph && !c->graph_failed) {
       cudaGraph_t g;
       if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        s = enqueue_sweep(c);
+        s = enqueue_sweep(c, mix);
         const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (s == MG_OK && e == cudaSuccess) {
-          if (cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) {
-            c->graph = nullptr;
+          if (cudaGraphInstantiate(&graph, g, 0) != cudaSuccess) {
+            graph = nullptr;
             c->graph_failed = true;
           }
           cudaGraphDestroy(g);
@@ -1185,10 +1195,10 @@ mg_status mg_sweep(mg_ctx* c, int64_t n) {
         (void)cudaGetLastError();
       }
     }
-    if (c->graph) {
-      MG_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
+    if (graph) {
+      MG_CUDA(c, cudaGraphLaunch(graph, c->stream));
     } else {
-      s = enqueue_sweep(c);
+      s = enqueue_sweep(c, mix);
       if (s != MG_OK) return s;
     }
     ++c->sweeps;
@@ -1207,14 +1217,15 @@ mg_status mg_sweep_timed(mg_ctx* c, int64_t n, double* ms_out) {
   cudaEvent_t ev[4];
   for (auto& e : ev) MG_CUDA(c, cudaEventCreate(&e));
   for (int64_t i = 0; i < n; ++i) {
+    const bool mix = mixing_sweep_next(c);
     MG_CUDA(c, cudaEventRecord(ev[0], c->stream));
-    mg_status s = c->precision == 32 ? enqueue_passes<float>(c, 1) : enqueue_passes<double>(c, 1);
+    mg_status s = c->precision == 32 ? enqueue_passes<float>(c, 1, mix) : enqueue_passes<double>(c, 1, mix);
     if (s != MG_OK) return s;
     MG_CUDA(c, cudaEventRecord(ev[1], c->stream));
-    s = c->precision == 32 ? enqueue_passes<float>(c, 2) : enqueue_passes<double>(c, 2);
+    s = c->precision == 32 ? enqueue_passes<float>(c, 2, mix) : enqueue_passes<double>(c, 2, mix);
     if (s != MG_OK) return s;
     MG_CUDA(c, cudaEventRecord(ev[2], c->stream));
-    s = c->precision == 32 ? enqueue_passes<float>(c, 4) : enqueue_passes<double>(c, 4);
+    s = c->precision == 32 ? enqueue_passes<float>(c, 4, mix) : enqueue_passes<double>(c, 4, mix);
     if (s != MG_OK) return s;
     MG_CUDA(c, cudaEventRecord(ev[3], c->stream));
     MG_CUDA(c, cudaEventSynchronize(ev[3]));
@@ -1441,6 +1452,7 @@ void mg_destroy(mg_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph_mix) cudaGraphExecDestroy(c->graph_mix);
   c->classes.clear();
   c->chains.clear();
   c->groups.clear();
