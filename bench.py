@@ -176,10 +176,28 @@ def cpu_baseline(seconds_budget=25.0):
                       "numpy FP64 single-threaded"}
 
 
+def tau_int(x) -> float:
+    """Integrated autocorrelation time of a trace (Sokal's automatic window:
+    sum the normalised autocorrelation up to the first lag k >= 5 tau)."""
+    x = np.asarray(x, dtype=np.float64) - np.mean(x)
+    n = len(x)
+    f = np.fft.rfft(x, 2 * n)
+    acf = np.fft.irfft(f * np.conj(f))[:n]
+    acf /= acf[0]
+    t = 1.0
+    for k in range(1, n // 2):
+        t += 2.0 * acf[k]
+        if k >= 5.0 * t:
+            break
+    return float(t)
+
+
 def run_other_workload(args):
     """Secondary workloads (not the headline line): the batching workload in
-    one persistent launch per sweep, the adjoint of 8 sweeps at 128^3 FP32, and
-    the plain FP64 sampler on the 128^3 grid with holes."""
+    one persistent launch per sweep, the adjoint of 8 sweeps at 128^3 FP32, the
+    plain FP64 sampler on the 128^3 grid with holes, mixing sweeps (Sec. 3.3)
+    on the 256^3 workload, and the P(k) autocorrelation of plain, mixing and
+    alternating sweeps."""
     import torch
     from paper_1402_1763_gb300 import Sampler
     stream = torch.cuda.Stream()
@@ -232,7 +250,63 @@ def run_other_workload(args):
         ms = ev[0].elapsed_time(ev[1]) / args.steps
         line.update(value=m.n ** 3 / (ms * 1e-3), ms_per_step=ms, dtype="f64",
                     config={"workload": w.name, "removed_fraction": m.removed_fraction})
-    g.close()
+    elif args.workload == "mixing-256":
+        w = mockgen.workload(3)
+        m = w.mocks[0]
+        g = Sampler.single(m.n, m.L, m.N, m.R, m.d, m.n_bins, 3, precision=32, n_chains=16, mixing=1,
+                           stream=stream.cuda_stream)
+        g.sweep(args.warmup)
+        g.sync()
+        ev[0].record(stream)
+        g.sweep(args.steps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / args.steps
+        per = g.sweep_timed(5) / 5
+        acc = np.mean([g.read_stats(c)["chi_b"][1:-1].mean() for c in range(16)])
+        line.update(value=16 * m.n ** 3 / (ms * 1e-3), ms_per_step=ms, dtype="f32",
+                    config={"workload": w.name + "-mixing-sweeps", "chains_per_gpu": 16,
+                            "l2": "inputs larger than L2 (1.08 GB chain state)"},
+                    per_pass_ms={"pass_yz": per[0], "pass_x_mixing": per[1], "sweep_counter": per[2]},
+                    acceptance_rate=float(acc))
+    elif args.workload == "mixing-acf":
+        # Fully observed 64^3 grid, constant noise N = 1 (R = 1): the shells
+        # run from S/N ~ 80 to ~0.2.  Integrated autocorrelation time of
+        # log P_b over 3000 sweeps after 300, for plain, mixing and
+        # alternating sweeps (the statistical efficiency claim of Sec. 3.3).
+        n, L, Nn = 64, 1000.0, 1.0
+        s_true = mockgen.gaussian_field(n, L, 9)
+        rng = np.random.default_rng(4)
+        N = np.full((n, n, n), Nn)
+        R = np.ones((n, n, n))
+        d = s_true + np.sqrt(Nn) * rng.standard_normal((n, n, n))
+        K, burn = 3000, 300
+        taus, snr = {}, None
+        t0 = time.perf_counter()
+        for kind, mix in (("plain", 0), ("mixing", 1), ("alternating", 2)):
+            g = Sampler.single(n, L, N, R, d, n // 4, 5, precision=32, mixing=mix, stream=stream.cuda_stream)
+            g.sweep(burn)
+            tr = np.empty((K, n // 4 + 1))
+            for k in range(K):
+                g.sweep(1)
+                tr[k] = g.read_pk(0)
+            nb = g.read_stats(0)["n_b"]
+            taus[kind] = [round(tau_int(np.log(tr[:, b])), 1) if nb[b] else 0.0 for b in range(tr.shape[1])]
+            if kind == "plain":
+                snr = (tr.mean(0) * n ** 3 / L ** 3 / Nn).round(3).tolist()
+            g.close()
+        g = None
+        low = [b for b in range(len(snr)) if snr[b] < 1.0]
+        line.update(metric="worst integrated autocorrelation time of log P_b over shells with S/N < 1 "
+                           "(alternating plain/mixing sweeps)",
+                    value=max(taus["alternating"][b] for b in low), unit="sweeps", higher_is_better=False,
+                    ms_per_step=(time.perf_counter() - t0) * 1e3 / (3 * (K + burn)), dtype="f32",
+                    config={"workload": "fully observed 64^3, N = 1, 16 shells", "sweeps": K, "burn_in": burn},
+                    s_over_n=snr, tau_plain=taus["plain"], tau_mixing=taus["mixing"],
+                    tau_alternating=taus["alternating"],
+                    worst_low_snr={k: max(v[b] for b in low) for k, v in taus.items()})
+    if g is not None:
+        g.close()
     print(json.dumps(line))
     return 0
 
@@ -245,7 +319,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="256-fp32-16chains",
-                    choices=["256-fp32-16chains", "batch-48chains", "adjoint-128", "fp64-128holes"])
+                    choices=["256-fp32-16chains", "batch-48chains", "adjoint-128", "fp64-128holes",
+                             "mixing-256", "mixing-acf"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = replicas.rank_world()
