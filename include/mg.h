@@ -75,7 +75,9 @@ typedef struct {
   const double* P0;       /* n_bins+1 starting powers shared by all chains, or
                              NULL for flat S_hat = 1 (P = V/M).               */
   int32_t record_every;   /* >0: accumulate per-voxel mean/variance of s and a
-                             P(k) trace every record_every-th sweep; 0 = off. */
+                             P(k) trace every record_every-th sweep of
+                             mg_sweep (see mg_read_pk_trace, mg_pk_acf,
+                             mg_pk_quantiles); 0 = off.                       */
   int32_t fix_P;          /* nonzero: hold P fixed (signal sampler only).     */
   int64_t timeout_cycles; /* budget of device-side waits in clock cycles;
                              0 = library default.                            */
@@ -193,6 +195,32 @@ mg_status mg_set_data(mg_ctx* ctx, int32_t group, const double* d);
  * restored before returning.  Synchronises. */
 mg_status mg_adjoint(mg_ctx* ctx, int32_t chain, int32_t K, const double* logP, const double* w, double* loss,
                      double* dlogP, double* dd);
+
+/* The recorded P(k) trace of one chain (record_every > 0: P after every
+ * record_every-th sweep of mg_sweep, kept on the device).  out: host array of
+ * max_records * (n_bins+1) doubles, record-major; the first
+ * min(records, max_records) rows are written.  *n_records (may be NULL)
+ * receives the number of records.  Synchronises. */
+mg_status mg_read_pk_trace(mg_ctx* ctx, int32_t chain, double* out, int64_t max_records, int64_t* n_records);
+
+/* Statistical efficiency of a chain's recorded P(k) (the correlation-length
+ * analysis of the paper's results section), computed on the device from the
+ * trace: per shell b the autocorrelation
+ *   C_n = [1/(R-n) sum_{i<R-n} (P_i - <P>)(P_{i+n} - <P>)] / Var(P),
+ * n = 0 .. max_lag (R records, Var with 1/R), into acf[b * (max_lag+1) + n]
+ * (host, (n_bins+1)*(max_lag+1) doubles), and the correlation length n_c[b] =
+ * the first lag n >= 1 with C_n < 0.1, or -1 if none up to max_lag (host,
+ * n_bins+1 int32).  A constant trace (a held empty shell) gives C_n = 1 and
+ * n_c = -1.  MG_EINVAL unless 0 <= max_lag < R.  Synchronises. */
+mg_status mg_pk_acf(mg_ctx* ctx, int32_t chain, int32_t max_lag, double* acf, int32_t* n_c);
+
+/* Posterior quantiles of each shell's P from the recorded trace, computed on
+ * the device (credible bands of the power spectrum): for q[i] in [0, 1],
+ * h = (R-1) q, k = floor(h), out[b * n_q + i] = x_(k) + (h - k)(x_(k+1) - x_(k))
+ * with x_(j) the j-th smallest of shell b's R recorded values.  q: host, n_q
+ * doubles; out: host, (n_bins+1)*n_q doubles.  MG_EINVAL without records.
+ * Cost O(R^2) per shell and quantile on the device.  Synchronises. */
+mg_status mg_pk_quantiles(mg_ctx* ctx, int32_t chain, int32_t n_q, const double* q, double* out);
 
 /* Sweep counter (Philox counter word 1 of the next sweep); mg_set_sweep_count
  * restores it when resuming from a checkpoint. */

@@ -12,8 +12,9 @@ Modules:
   sampler  tau and N~ (Sec. 2), Alg. 1, Alg. 2 on shells, the chain driver
   adjoint  torch FP64 autograd of a fixed-P chain of sweeps (differentiation workload)
   mixing   the mixing sampler of Sec. 3.3 (Alg. 3) on k-shells
+  summary  correlation length and quantiles of a recorded P(k) trace
 
 Every function is pinned by CPU tests (tests/test_oracle_*.py) against values
 the paper or the mathematics fixes, not against the oracle itself.
 """
-from . import philox, bins, sampler, mixing  # noqa: F401
+from . import philox, bins, sampler, mixing, summary  # noqa: F401

@@ -87,6 +87,9 @@ def library():
         "mg_philox": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int64,
                                 _P, _P]),
         "mg_shell_sums_noalloc": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P]),
+        "mg_read_pk_trace": (C.c_int, [_P, C.c_int32, _D, C.c_int64, C.POINTER(C.c_int64)]),
+        "mg_pk_acf": (C.c_int, [_P, C.c_int32, C.c_int32, _D, C.POINTER(C.c_int32)]),
+        "mg_pk_quantiles": (C.c_int, [_P, C.c_int32, C.c_int32, _D, _D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -188,6 +191,24 @@ def mg_read_s(ctx, chain: int, out_ptr: int, out_is_device: bool):
 
 def mg_read_pk(ctx, chain: int, out: np.ndarray):
     _check(library().mg_read_pk(ctx, int(chain), _dptr(out)), ctx)
+
+
+def mg_read_pk_trace(ctx, chain: int, out, max_records: int) -> int:
+    """Fill out (max_records x (n_bins+1) doubles) with the recorded P(k)
+    trace; returns the number of records."""
+    n = C.c_int64(0)
+    _check(library().mg_read_pk_trace(ctx, int(chain), _dptr(out) if out is not None else None,
+                                      int(max_records), C.byref(n)), ctx)
+    return int(n.value)
+
+
+def mg_pk_acf(ctx, chain: int, max_lag: int, acf: np.ndarray, n_c: np.ndarray):
+    _check(library().mg_pk_acf(ctx, int(chain), int(max_lag), _dptr(acf),
+                               n_c.ctypes.data_as(C.POINTER(C.c_int32))), ctx)
+
+
+def mg_pk_quantiles(ctx, chain: int, q: np.ndarray, out: np.ndarray):
+    _check(library().mg_pk_quantiles(ctx, int(chain), int(q.size), _dptr(q), _dptr(out)), ctx)
 
 
 def mg_read_stats(ctx, chain: int, stats: MgStats):
@@ -334,6 +355,31 @@ class Sampler:
 
     def sweep_timed(self, n=1) -> np.ndarray:
         return mg_sweep_timed(self.ctx, n)
+
+    def pk_trace(self, chain=0) -> np.ndarray:
+        """The recorded P(k) of one chain, shape (records, n_bins+1)."""
+        nb = self.info(chain)[1] + 1
+        R = mg_read_pk_trace(self.ctx, chain, None, 0)
+        out = np.empty((R, nb))
+        if R:
+            mg_read_pk_trace(self.ctx, chain, out, R)
+        return out
+
+    def pk_acf(self, max_lag, chain=0):
+        """(acf (n_bins+1, max_lag+1), n_c (n_bins+1)) from the recorded trace."""
+        nb = self.info(chain)[1] + 1
+        acf = np.empty((nb, int(max_lag) + 1))
+        nc = np.empty(nb, dtype=np.int32)
+        mg_pk_acf(self.ctx, chain, max_lag, acf, nc)
+        return acf, nc
+
+    def pk_quantiles(self, q, chain=0) -> np.ndarray:
+        """Quantiles of each shell's recorded P, shape (n_bins+1, len(q))."""
+        q = _f64(q)
+        nb = self.info(chain)[1] + 1
+        out = np.empty((nb, q.size))
+        mg_pk_quantiles(self.ctx, chain, q, out)
+        return out
 
     def sync(self):
         mg_sync(self.ctx)

@@ -48,6 +48,8 @@ struct Chain {
   int group = 0;
   uint32_t chain_id = 0;
   std::shared_ptr<DevBuf> main, nyq, coef, mscale, partial, P, sig, chi, mean, m2;
+  std::shared_ptr<DevBuf> trace;  // [records][B+1] P after every record_every-th sweep
+  long long trace_cap = 0;        // records the trace buffer holds
 };
 
 // All chains of one grid size are launched together.
@@ -825,6 +827,23 @@ mg_status record_stats(mg_ctx* c) {
     welford_kernel<T><<<1024, 256, 0, c->stream>>>(s, static_cast<double*>(c->chains[ci].mean->p),
                                                    static_cast<double*>(c->chains[ci].m2->p), g.M, inv);
     MG_CUDA(c, cudaGetLastError());
+    // append P to the chain's trace (the buffer doubles when full)
+    Chain& ch = c->chains[ci];
+    const size_t row = size_t(g.B + 1) * sizeof(double);
+    if (c->records > ch.trace_cap) {
+      const long long cap = std::max<long long>(64, 2 * ch.trace_cap);
+      cudaError_t e;
+      auto nb = dalloc(size_t(cap) * row, &e);
+      MG_CUDA(c, e);
+      if (ch.trace && ch.trace_cap > 0)
+        MG_CUDA(c, cudaMemcpyAsync(nb->p, ch.trace->p, size_t(ch.trace_cap) * row, cudaMemcpyDeviceToDevice,
+                                   c->stream));
+      MG_CUDA(c, cudaStreamSynchronize(c->stream));
+      ch.trace = nb;
+      ch.trace_cap = cap;
+    }
+    MG_CUDA(c, cudaMemcpyAsync(static_cast<char*>(ch.trace->p) + size_t(c->records - 1) * row, ch.P->p, row,
+                               cudaMemcpyDeviceToDevice, c->stream));
     MG_CUDA(c, cudaStreamSynchronize(c->stream));
   }
   return MG_OK;
@@ -1422,6 +1441,71 @@ mg_status mg_set_sweep_count(mg_ctx* c, int64_t sweeps) {
   MG_CUDA(c, cudaMemcpyAsync(c->d_sweep->p, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream));
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
   c->sweeps = sweeps;
+  return MG_OK;
+}
+
+mg_status mg_read_pk_trace(mg_ctx* c, int32_t chain, double* out, int64_t max_records, int64_t* n_records) {
+  if (!c) return MG_EINVAL;
+  if (c->sticky != MG_OK) return c->sticky;
+  if (!valid_chain(c, chain)) return fail(c, MG_EINVAL, "chain index out of range");
+  if (max_records < 0) return fail(c, MG_EINVAL, "max_records must be >= 0");
+  const Chain& ch = c->chains[chain];
+  const size_t row = size_t(c->groups[ch.group].B + 1) * sizeof(double);
+  const long long n = std::min<long long>(c->records, max_records);
+  if (n_records) *n_records = c->records;
+  if (n > 0) {
+    if (!out) return fail(c, MG_EINVAL, "null output");
+    MG_CUDA(c, cudaMemcpyAsync(out, ch.trace->p, size_t(n) * row, cudaMemcpyDeviceToHost, c->stream));
+    MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return MG_OK;
+}
+
+mg_status mg_pk_acf(mg_ctx* c, int32_t chain, int32_t max_lag, double* acf, int32_t* n_c) {
+  if (!c || !acf || !n_c) return MG_EINVAL;
+  if (c->sticky != MG_OK) return c->sticky;
+  if (!valid_chain(c, chain)) return fail(c, MG_EINVAL, "chain index out of range");
+  if (max_lag < 0 || max_lag >= c->records)
+    return fail(c, MG_EINVAL, "need 0 <= max_lag < recorded P(k) samples (record_every > 0)");
+  const Chain& ch = c->chains[chain];
+  const int B1 = c->groups[ch.group].B + 1;
+  cudaError_t e;
+  auto da = dalloc(size_t(B1) * (max_lag + 1) * sizeof(double), &e);
+  MG_CUDA(c, e);
+  auto dn = dalloc(size_t(B1) * sizeof(int), &e);
+  MG_CUDA(c, e);
+  pk_acf_kernel<<<B1, 256, 0, c->stream>>>(static_cast<const double*>(ch.trace->p), c->records, B1, max_lag,
+                                           static_cast<double*>(da->p), static_cast<int*>(dn->p));
+  MG_CUDA(c, cudaGetLastError());
+  MG_CUDA(c, cudaMemcpyAsync(acf, da->p, size_t(B1) * (max_lag + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+  MG_CUDA(c, cudaMemcpyAsync(n_c, dn->p, size_t(B1) * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+mg_status mg_pk_quantiles(mg_ctx* c, int32_t chain, int32_t n_q, const double* q, double* out) {
+  if (!c || !q || !out) return MG_EINVAL;
+  if (c->sticky != MG_OK) return c->sticky;
+  if (!valid_chain(c, chain)) return fail(c, MG_EINVAL, "chain index out of range");
+  if (n_q < 1 || n_q > 65535) return fail(c, MG_EINVAL, "1 <= n_q <= 65535");
+  for (int i = 0; i < n_q; ++i)
+    if (!(q[i] >= 0.0 && q[i] <= 1.0)) return fail(c, MG_EINVAL, "quantiles must lie in [0, 1]");
+  if (c->records < 1) return fail(c, MG_EINVAL, "no recorded P(k) samples (record_every > 0)");
+  const Chain& ch = c->chains[chain];
+  const int B1 = c->groups[ch.group].B + 1;
+  cudaError_t e;
+  auto dq = dalloc(size_t(n_q) * sizeof(double), &e);
+  MG_CUDA(c, e);
+  auto dout = dalloc(size_t(B1) * n_q * sizeof(double), &e);
+  MG_CUDA(c, e);
+  MG_CUDA(c, cudaMemcpyAsync(dq->p, q, size_t(n_q) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  pk_quantile_kernel<<<dim3(unsigned(B1), unsigned(n_q)), 256, 0, c->stream>>>(
+      static_cast<const double*>(ch.trace->p), c->records, B1, static_cast<const double*>(dq->p),
+      static_cast<double*>(dout->p));
+  MG_CUDA(c, cudaGetLastError());
+  MG_CUDA(c, cudaMemcpyAsync(out, dout->p, size_t(B1) * n_q * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
   return MG_OK;
 }
 

@@ -320,11 +320,80 @@ __global__ void welford_kernel(const T* __restrict__ s, double* __restrict__ mea
   }
 }
 
-// Append each chain's P to its trace: trace[chain][slot][b].
-__global__ void trace_kernel(const DrawDev* __restrict__ chains, double* const* traces, int slot) {
-  const DrawDev cd = chains[blockIdx.x];
-  double* tr = traces[blockIdx.x];
-  for (int b = threadIdx.x; b <= cd.B; b += blockDim.x) tr[size_t(slot) * (cd.B + 1) + b] = cd.P[b];
+// Efficiency analysis of a recorded P(k) trace (Sec. 4, statistical
+// efficiency; trace[r][b], r < R records, B1 shells).  One CTA of 256 threads
+// per shell; sums are formed per thread in a fixed stride order and combined
+// by a fixed tree, so results are deterministic.
+__device__ inline double block_sum_256(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Autocorrelation of shell b's amplitudes,
+//   C_n = [1/(R-n) sum_{i<R-n} (P_i - m)(P_{i+n} - m)] / var,
+// m and var the trace mean and (1/R) variance, for n = 0 .. max_lag
+// (max_lag < R), and the correlation length n_c = the first n >= 1 with
+// C_n < 0.1 (-1 if none up to max_lag).  A constant trace (held shell) has
+// C_n = 1 and n_c = -1.
+__global__ void pk_acf_kernel(const double* __restrict__ trace, long long R, int B1, int max_lag,
+                              double* __restrict__ acf, int* __restrict__ nc) {
+  __shared__ double red[256];
+  const int b = blockIdx.x;
+  double s = 0.0;
+  for (long long r = threadIdx.x; r < R; r += 256) s += trace[r * B1 + b];
+  const double m = block_sum_256(s, red) / double(R);
+  s = 0.0;
+  for (long long r = threadIdx.x; r < R; r += 256) {
+    const double d = trace[r * B1 + b] - m;
+    s += d * d;
+  }
+  const double var = block_sum_256(s, red) / double(R);
+  int first = -1;
+  for (int n = 0; n <= max_lag; ++n) {
+    double c = 1.0;
+    if (var > 0.0) {
+      s = 0.0;
+      for (long long r = threadIdx.x; r + n < R; r += 256) s += (trace[r * B1 + b] - m) * (trace[(r + n) * B1 + b] - m);
+      c = block_sum_256(s, red) / (double(R - n) * var);
+    }
+    if (threadIdx.x == 0) {
+      acf[size_t(b) * (max_lag + 1) + n] = c;
+      if (first < 0 && n >= 1 && c < 0.1) first = n;
+    }
+  }
+  if (threadIdx.x == 0) nc[b] = first;
+}
+
+// Quantile q of shell b's amplitudes with linear interpolation between order
+// statistics: h = (R-1) q, k = floor(h), value x_(k) + (h - k)(x_(k+1) - x_(k)).
+// The order statistic of rank k is found by ranking every element
+// (rank = #{x_j < x_i} + #{j < i : x_j = x_i}, a permutation).  Grid: (B1, n_q).
+__global__ void pk_quantile_kernel(const double* __restrict__ trace, long long R, int B1,
+                                   const double* __restrict__ q, double* __restrict__ out) {
+  __shared__ double xk[2];
+  const int b = blockIdx.x, iq = blockIdx.y;
+  const double h = double(R - 1) * q[iq];
+  const long long k = (long long)floor(h);
+  const long long k1 = k + 1 < R ? k + 1 : k;
+  for (long long i = threadIdx.x; i < R; i += blockDim.x) {
+    const double xi = trace[i * B1 + b];
+    long long rank = 0;
+    for (long long j = 0; j < R; ++j) {
+      const double xj = trace[j * B1 + b];
+      rank += (xj < xi) || (xj == xi && j < i);
+    }
+    if (rank == k) xk[0] = xi;
+    if (rank == k1) xk[1] = xi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) out[size_t(b) * gridDim.y + iq] = xk[0] + (h - double(k)) * (xk[1] - xk[0]);
 }
 
 __global__ void philox_fill_kernel(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
