@@ -350,7 +350,7 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
     }
     // Messenger constants: only the row's observed z-range is stored; a
     // group of four voxels outside it has b = 1, c = 0 and needs no load.
-    // Each group's constants are loaded one iteration ahead.
+    // Each group's constants are loaded ahead of their use (L2 latency).
     uint32_t lo = 0, hi = 0;
     const typename VT<T>::c2* brow = nullptr;
     if constexpr (MODE == kModeSweep) {
@@ -367,8 +367,13 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
         for (int k = 0; k < 4; ++k) out[k] = {T(1), T(0)};
       }
     };
-    cx<T> bc_next[4];
-    if constexpr (MODE == kModeSweep) load_group(2 * pp, bc_next);
+    // (FP32 only: in FP64 the second group in flight costs spills)
+    constexpr int kAhead = sizeof(T) == 4 ? 2 : 1;
+    cx<T> bc_next[4], bc_next2[4];
+    if constexpr (MODE == kModeSweep) {
+      load_group(2 * pp, bc_next);
+      if (kAhead == 2 && Q2 > 1) load_group(2 * (pp + P2), bc_next2);
+    }
 #pragma unroll
     for (int q = 0; q < Q2; ++q) {
       const int z0 = 2 * (pp + P2 * q);  // voxels z0 .. z0+3
@@ -377,7 +382,13 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
       if constexpr (MODE == kModeSweep) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) bcv[k] = bc_next[k];
-        if (q + 1 < Q2) load_group(2 * (pp + P2 * (q + 1)), bc_next);
+        if constexpr (kAhead == 2) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) bc_next[k] = bc_next2[k];
+          if (q + 2 < Q2) load_group(2 * (pp + P2 * (q + 2)), bc_next2);
+        } else {
+          if (q + 1 < Q2) load_group(2 * (pp + P2 * (q + 1)), bc_next);
+        }
       }
       if constexpr (MODE == kModeMaterialize) {
         T* o = cd.s_out + i0;
