@@ -419,6 +419,28 @@ def main():
         fp64 = {"value": M / (ms64 * 1e-3), "unit": UNIT, "ms_per_sweep": ms64,
                 "config": "plain FP64, 1 chain, same 256^3 data"}
 
+    # comparison only: the library transforms (cuFFT via torch.fft) of one
+    # sweep's work, one forward R2C and one inverse C2R 3D FFT per chain, with
+    # none of the sweep's draws, shell sums or messenger constants
+    cufft = None
+    if rank == 0:
+        x = torch.randn(N_CHAINS, N_GRID, N_GRID, N_GRID, device="cuda")
+        for _ in range(3):
+            y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=x.shape[1:], dim=(1, 2, 3))
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        kc = 10
+        c0.record()
+        for _ in range(kc):
+            y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=x.shape[1:], dim=(1, 2, 3))
+        c1.record()
+        torch.cuda.synchronize()
+        cufft = {"ms_fwd_inv_16chains": c0.elapsed_time(c1) / kc,
+                 "note": "torch.fft (cuFFT) rfftn + irfftn of 16 x 256^3 FP32 fields: the transforms alone of "
+                         "one sweep, timed for comparison only (not used by the sampler)"}
+        del x, y
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -435,6 +457,7 @@ def main():
         "sweeps_per_s": 1e3 / ms,
         "chain_sweeps_per_s": world * N_CHAINS * 1e3 / ms,
         "fp64_single_chain": fp64,
+        "cufft_comparison": cufft,
         "batched_fp32_over_fp64": (value / world) / fp64["value"] if fp64 else None,
         "per_pass_ms": {"pass_yz": per[0], "pass_x": per[1], "shell_draw": per[2]},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
