@@ -222,6 +222,17 @@ mg_status mg_pk_acf(mg_ctx* ctx, int32_t chain, int32_t max_lag, double* acf, in
  * Cost O(R^2) per shell and quantile on the device.  Synchronises. */
 mg_status mg_pk_quantiles(mg_ctx* ctx, int32_t chain, int32_t n_q, const double* q, double* out);
 
+/* Gelman-Rubin convergence diagnostic of P(k) across chains (the use the
+ * independent chains of Sec. 3.4 are put to), on the device from the recorded
+ * traces of chains first_chain .. first_chain+n_chains-1 (2 <= n_chains <= 256,
+ * all with the same shells), using records burn .. R-1 (at least 2): per
+ * shell, with chain means m_j and unbiased variances v_j over those n
+ * records, W = mean_j v_j, B = n/(n_chains-1) sum_j (m_j - mean m)^2 and
+ * var+ = (n-1)/n W + B/n, rhat[b] = sqrt(var+ / W) (host, n_bins+1 doubles;
+ * 1 where every chain is constant and equal, +inf where they are constant
+ * and differ).  Synchronises. */
+mg_status mg_pk_rhat(mg_ctx* ctx, int32_t first_chain, int32_t n_chains, int64_t burn, double* rhat);
+
 /* Sweep counter (Philox counter word 1 of the next sweep); mg_set_sweep_count
  * restores it when resuming from a checkpoint. */
 mg_status mg_get_sweep_count(mg_ctx* ctx, int64_t* out);

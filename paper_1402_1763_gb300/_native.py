@@ -90,6 +90,7 @@ def library():
         "mg_read_pk_trace": (C.c_int, [_P, C.c_int32, _D, C.c_int64, C.POINTER(C.c_int64)]),
         "mg_pk_acf": (C.c_int, [_P, C.c_int32, C.c_int32, _D, C.POINTER(C.c_int32)]),
         "mg_pk_quantiles": (C.c_int, [_P, C.c_int32, C.c_int32, _D, _D]),
+        "mg_pk_rhat": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int64, _D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -209,6 +210,10 @@ def mg_pk_acf(ctx, chain: int, max_lag: int, acf: np.ndarray, n_c: np.ndarray):
 
 def mg_pk_quantiles(ctx, chain: int, q: np.ndarray, out: np.ndarray):
     _check(library().mg_pk_quantiles(ctx, int(chain), int(q.size), _dptr(q), _dptr(out)), ctx)
+
+
+def mg_pk_rhat(ctx, first_chain: int, n_chains: int, burn: int, out: np.ndarray):
+    _check(library().mg_pk_rhat(ctx, int(first_chain), int(n_chains), int(burn), _dptr(out)), ctx)
 
 
 def mg_read_stats(ctx, chain: int, stats: MgStats):
@@ -372,6 +377,15 @@ class Sampler:
         nc = np.empty(nb, dtype=np.int32)
         mg_pk_acf(self.ctx, chain, max_lag, acf, nc)
         return acf, nc
+
+    def pk_rhat(self, first_chain=0, n_chains=None, burn=0) -> np.ndarray:
+        """Gelman-Rubin R-hat per shell over chains first_chain .. +n_chains-1
+        (default: all chains of the context) from their recorded traces."""
+        if n_chains is None:
+            n_chains = self.info(0)[2] - first_chain
+        out = np.empty(self.info(first_chain)[1] + 1)
+        mg_pk_rhat(self.ctx, first_chain, n_chains, burn, out)
+        return out
 
     def pk_quantiles(self, q, chain=0) -> np.ndarray:
         """Quantiles of each shell's recorded P, shape (n_bins+1, len(q))."""

@@ -1509,6 +1509,34 @@ mg_status mg_pk_quantiles(mg_ctx* c, int32_t chain, int32_t n_q, const double* q
   return MG_OK;
 }
 
+mg_status mg_pk_rhat(mg_ctx* c, int32_t first_chain, int32_t n_chains, int64_t burn, double* rhat) {
+  if (!c || !rhat) return MG_EINVAL;
+  if (c->sticky != MG_OK) return c->sticky;
+  if (n_chains < 2 || n_chains > 256) return fail(c, MG_EINVAL, "2 <= n_chains <= 256");
+  if (!valid_chain(c, first_chain) || !valid_chain(c, first_chain + n_chains - 1))
+    return fail(c, MG_EINVAL, "chain index out of range");
+  if (burn < 0 || c->records - burn < 2) return fail(c, MG_EINVAL, "need at least 2 recorded samples after burn");
+  const int B = c->groups[c->chains[first_chain].group].B;
+  std::vector<const double*> ptrs(n_chains);
+  for (int j = 0; j < n_chains; ++j) {
+    const Chain& ch = c->chains[first_chain + j];
+    if (c->groups[ch.group].B != B) return fail(c, MG_EINVAL, "chains must have the same shells");
+    ptrs[j] = static_cast<const double*>(ch.trace->p);
+  }
+  cudaError_t e;
+  auto dp = dalloc(ptrs.size() * sizeof(double*), &e);
+  MG_CUDA(c, e);
+  auto dout = dalloc(size_t(B + 1) * sizeof(double), &e);
+  MG_CUDA(c, e);
+  MG_CUDA(c, cudaMemcpyAsync(dp->p, ptrs.data(), ptrs.size() * sizeof(double*), cudaMemcpyHostToDevice, c->stream));
+  pk_rhat_kernel<<<B + 1, 256, 0, c->stream>>>(static_cast<const double* const*>(dp->p), n_chains, c->records, burn,
+                                               B + 1, static_cast<double*>(dout->p));
+  MG_CUDA(c, cudaGetLastError());
+  MG_CUDA(c, cudaMemcpyAsync(rhat, dout->p, size_t(B + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
 mg_status mg_chain_info(mg_ctx* c, int32_t chain, int32_t* n, int32_t* n_bins, int32_t* n_chains) {
   if (!c) return MG_EINVAL;
   if (n_chains) *n_chains = int32_t(c->chains.size());

@@ -346,9 +346,11 @@ __global__ void pk_acf_kernel(const double* __restrict__ trace, long long R, int
                               double* __restrict__ acf, int* __restrict__ nc) {
   __shared__ double red[256];
   const int b = blockIdx.x;
+  // mean about the first sample, so that a constant trace has exactly zero variance
+  const double x0 = trace[b];
   double s = 0.0;
-  for (long long r = threadIdx.x; r < R; r += 256) s += trace[r * B1 + b];
-  const double m = block_sum_256(s, red) / double(R);
+  for (long long r = threadIdx.x; r < R; r += 256) s += trace[r * B1 + b] - x0;
+  const double m = x0 + block_sum_256(s, red) / double(R);
   s = 0.0;
   for (long long r = threadIdx.x; r < R; r += 256) {
     const double d = trace[r * B1 + b] - m;
@@ -394,6 +396,52 @@ __global__ void pk_quantile_kernel(const double* __restrict__ trace, long long R
   }
   __syncthreads();
   if (threadIdx.x == 0) out[size_t(b) * gridDim.y + iq] = xk[0] + (h - double(k)) * (xk[1] - xk[0]);
+}
+
+// Gelman-Rubin potential scale reduction of shell b's amplitudes over m
+// chains' traces (records burn .. R-1, n = R - burn >= 2 per chain): chain
+// means and unbiased variances, W = mean of the variances,
+// B = n/(m-1) sum_j (mean_j - mean)^2, var+ = (n-1)/n W + B/n,
+// R-hat = sqrt(var+ / W); 1 for a shell whose chains are all constant and
+// equal, +inf if they are constant but differ.  One CTA per shell.
+__global__ void pk_rhat_kernel(const double* const* __restrict__ traces, int m, long long R, long long burn,
+                               int B1, double* __restrict__ out) {
+  __shared__ double red[256], mj[256], vj[256];  // m <= 256
+  const int b = blockIdx.x;
+  const long long n = R - burn;
+  for (int j = 0; j < m; ++j) {
+    const double* tr = traces[j];
+    const double x0 = tr[burn * B1 + b];  // mean about the first sample (exact for a constant chain)
+    double s = 0.0;
+    for (long long r = burn + threadIdx.x; r < R; r += 256) s += tr[r * B1 + b] - x0;
+    const double mean_j = x0 + block_sum_256(s, red) / double(n);
+    s = 0.0;
+    for (long long r = burn + threadIdx.x; r < R; r += 256) {
+      const double d = tr[r * B1 + b] - mean_j;
+      s += d * d;
+    }
+    const double var_j = block_sum_256(s, red) / double(n - 1);
+    if (threadIdx.x == 0) {
+      mj[j] = mean_j;
+      vj[j] = var_j;
+    }
+  }
+  if (threadIdx.x != 0) return;
+  double mean = 0.0, W = 0.0;
+  for (int j = 0; j < m; ++j) {
+    mean += mj[j];
+    W += vj[j];
+  }
+  mean /= m;
+  W /= m;
+  double ss = 0.0;
+  for (int j = 0; j < m; ++j) ss += (mj[j] - mean) * (mj[j] - mean);
+  const double Bv = double(n) / double(m - 1) * ss;
+  const double vplus = double(n - 1) / double(n) * W + Bv / double(n);
+  double r;
+  if (W > 0.0) r = sqrt(vplus / W);
+  else r = Bv > 0.0 ? INFINITY : 1.0;
+  out[b] = r;
 }
 
 __global__ void philox_fill_kernel(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,

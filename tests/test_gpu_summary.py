@@ -7,6 +7,7 @@ of the paper's efficiency analysis, posterior quantiles), through the C ABI.
 * mg_pk_acf and mg_pk_quantiles against the oracle's definitions applied to
   the trace read back (relative 1e-12; correlation lengths equal).
 * With record_every = 3 only every third sweep is recorded.
+* mg_pk_rhat over the chains against the oracle's Gelman-Rubin definition.
 * Invalid lags and quantiles, and summaries without records, are MG_EINVAL.
 """
 import numpy as np
@@ -46,6 +47,21 @@ def test_trace_acf_and_quantiles(precision, mixing):
             np.testing.assert_array_equal(nc, nc_o)
             q = [0.025, 0.16, 0.5, 0.84, 0.975, 0.0, 1.0]
             np.testing.assert_allclose(g.pk_quantiles(q, c), summary.quantiles(tr, q), rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("mixing", [0, 1])
+def test_rhat_across_chains(mixing):
+    need_gpu()
+    from oracle import summary
+    from paper_1402_1763_gb300 import Sampler
+    m = mockgen.make_mock(16, seed=6, n_bins=6, sigma_n=0.5)
+    with Sampler.single(m.n, m.L, m.N, m.R, m.d, 6, 9, precision=64, n_chains=4, record_every=1,
+                        mixing=mixing) as g:
+        g.sweep(120)
+        traces = [g.pk_trace(c) for c in range(4)]
+        for burn in (0, 40):
+            np.testing.assert_allclose(g.pk_rhat(0, 4, burn), summary.rhat(traces, burn), rtol=1e-12)
+        np.testing.assert_allclose(g.pk_rhat(1, 2, 10), summary.rhat(traces[1:3], 10), rtol=1e-12)
 
 
 def test_record_every_three():

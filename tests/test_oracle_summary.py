@@ -7,6 +7,8 @@
 * A constant trace: C_n = 1 and n_c = -1.
 * Quantiles of a shuffled 0 .. R-1 are q (R - 1) exactly, min and max at q = 0
   and 1.
+* Gelman-Rubin R-hat: a hand-computed two-chain case; ~1 for chains from one
+  distribution, > 1 when their means differ; the constant-chain conventions.
 """
 import numpy as np
 
@@ -48,3 +50,24 @@ def test_quantiles_of_a_permutation():
     tr = np.stack([rng.permutation(R), rng.permutation(R)], axis=1).astype(np.float64)
     q = np.array([0.0, 0.025, 0.16, 0.5, 0.84, 0.975, 1.0])
     np.testing.assert_allclose(summary.quantiles(tr, q), np.tile(q * (R - 1), (2, 1)), rtol=0, atol=1e-9)
+
+
+def test_rhat_hand_computed_case():
+    # chains (0, 2) and (2, 4): n = 2, W = 2, B = 4, var+ = 3, R-hat = sqrt(3/2)
+    a = np.array([[0.0], [2.0]])
+    b = np.array([[2.0], [4.0]])
+    np.testing.assert_allclose(summary.rhat([a, b]), [np.sqrt(1.5)], rtol=1e-15)
+
+
+def test_rhat_limits():
+    rng = np.random.default_rng(11)
+    same = [rng.standard_normal((20000, 2)) for _ in range(4)]
+    r = summary.rhat(same)
+    assert np.all(np.abs(r - 1.0) < 0.01)
+    shifted = [t + np.array([3.0 * k, 0.0]) for k, t in enumerate(same)]
+    r2 = summary.rhat(shifted)
+    assert r2[0] > 3.0 and abs(r2[1] - 1.0) < 0.01
+    const = [np.full((10, 2), 5.0), np.full((10, 2), 5.0)]
+    assert list(summary.rhat(const)) == [1.0, 1.0]
+    differ = [np.full((10, 1), 5.0), np.full((10, 1), 6.0)]
+    assert np.isinf(summary.rhat(differ)[0])
