@@ -105,6 +105,13 @@ typedef struct {
                              others plain.  0: plain sweeps.  Not with
                              persistent (MG_EUNSUPPORTED) or fix_P
                              (MG_EINVAL).  Default 0.                        */
+  double start_dispersion; /* >= 0.  > 0: over-dispersed starts (Sec. 3.4 runs
+                             independent chains from over-dispersed initial
+                             conditions): chain c starts at
+                             P_b = P0_b exp(start_dispersion z_b) with z_b the
+                             first Box-Muller normal of Philox call
+                             (b, 0, chain id, 2).  0: every chain starts at
+                             P0.  Default 0.                                 */
 } mg_options;
 
 /* Chain statistics (mg_read_stats). Arrays are caller-owned with the sizes

@@ -34,6 +34,7 @@ MASK32 = np.uint64(0xFFFFFFFF)
 
 STREAM_MESSENGER = 0
 STREAM_MODES = 1
+STREAM_START = 2   # over-dispersed starting powers (sampler.Chains)
 STREAM_MIXING = 4  # the mixing sampler's per-shell proposals (oracle/mixing.py)
 
 

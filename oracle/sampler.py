@@ -282,7 +282,7 @@ class Chains:
     """
 
     def __init__(self, prob: Problem, seed: int, chain_ids: Sequence[int],
-                 P0: Optional[np.ndarray] = None, fix_P: bool = False):
+                 P0: Optional[np.ndarray] = None, fix_P: bool = False, start_dispersion: float = 0.0):
         self.prob = prob
         self.seed = int(seed)
         self.chain_ids = list(chain_ids)
@@ -292,6 +292,14 @@ class Chains:
         if P0 is None:
             P0 = np.full(B1, prob.V / prob.M)
         self.P = np.tile(np.asarray(P0, dtype=np.float64).reshape(1, B1), (C, 1))
+        if start_dispersion > 0.0:
+            # over-dispersed starts (Sec. 3.4): P_b * exp(sigma z_b), z_b from
+            # Philox call (b, 0, chain, 2)
+            b = np.arange(B1, dtype=np.uint64)[None, :]
+            cid = np.asarray(self.chain_ids, dtype=np.uint64)[:, None]
+            w = ph.philox4x32_10(b, 0, cid, ph.STREAM_START, self.seed)
+            z = ph.box_muller(w[0], w[1])[0]
+            self.P = self.P * np.exp(start_dispersion * z)
         self.fix_P = fix_P
         self.sweeps_done = 0
         self.last_sig = None

@@ -28,7 +28,7 @@ class MgOptions(C.Structure):
                 ("record_every", C.c_int32), ("fix_P", C.c_int32),
                 ("timeout_cycles", C.c_int64), ("cuda_stream", C.c_void_p),
                 ("yz_cluster", C.c_int32), ("persistent", C.c_int32), ("autotune", C.c_int32),
-                ("mixing", C.c_int32)]
+                ("mixing", C.c_int32), ("start_dispersion", C.c_double)]
 
 
 class MgStats(C.Structure):
@@ -311,7 +311,8 @@ class Sampler:
 
     @staticmethod
     def _opts(precision, n_chains, chain_id0, tau_scale, P0, record_every, fix_P, stream,
-              yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0, mixing=False):
+              yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0, mixing=False,
+              start_dispersion=0.0):
         o = mg_options_init()
         o.precision = int(precision)
         o.n_chains = int(n_chains)
@@ -329,14 +330,16 @@ class Sampler:
         o.autotune = int(bool(autotune))
         o.timeout_cycles = int(timeout_cycles)
         o.mixing = int(mixing)  # False/True, or 2 to alternate plain and mixing sweeps
+        o.start_dispersion = float(start_dispersion)
         return o, keep
 
     @classmethod
     def single(cls, n, L, N, R, d, n_bins, seed, precision=64, n_chains=1, chain_id0=0,
                tau_scale=1.0, P0=None, record_every=0, fix_P=False, k_edges=None, stream=0,
-               yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0, mixing=False):
+               yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0, mixing=False,
+               start_dispersion=0.0):
         o, keep = cls._opts(precision, n_chains, chain_id0, tau_scale, P0, record_every, fix_P, stream,
-                            yz_cluster, persistent, autotune, timeout_cycles, mixing)
+                            yz_cluster, persistent, autotune, timeout_cycles, mixing, start_dispersion)
         ctx = mg_init(n, L, N, R, d, n_bins, seed, o, k_edges)
         del keep
         return cls(ctx, precision)
@@ -344,9 +347,10 @@ class Sampler:
     @classmethod
     def batch(cls, ns, Ls, Ns, Rs, ds, n_bins, seeds, precision=32, n_chains=1, chain_id0=0,
               tau_scale=1.0, P0=None, record_every=0, fix_P=False, k_edges=None, stream=0,
-              yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0, mixing=False):
+              yz_cluster=0, persistent=False, autotune=False, timeout_cycles=0, mixing=False,
+              start_dispersion=0.0):
         o, keep = cls._opts(precision, n_chains, chain_id0, tau_scale, P0, record_every, fix_P, stream,
-                            yz_cluster, persistent, autotune, timeout_cycles, mixing)
+                            yz_cluster, persistent, autotune, timeout_cycles, mixing, start_dispersion)
         ctx = mg_init_batch(ns, Ls, Ns, Rs, ds, n_bins, seeds, o, k_edges)
         del keep
         return cls(ctx, precision)

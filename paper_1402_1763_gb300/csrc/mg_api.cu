@@ -1019,6 +1019,12 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
       if (opt->P0)
         for (int b = 0; b <= gg.B; ++b) P0[b] = opt->P0[b];
       MG_CUDA(c, cudaMemcpy(ch.P->p, P0.data(), P0.size() * sizeof(double), cudaMemcpyHostToDevice));
+      if (opt->start_dispersion > 0.0) {
+        disperse_start_kernel<<<1, 256, 0, c->stream>>>(static_cast<double*>(ch.P->p), gg.B + 1,
+                                                        opt->start_dispersion, uint32_t(gg.seed & 0xffffffffu),
+                                                        uint32_t(gg.seed >> 32), ch.chain_id);
+        MG_CUDA(c, cudaGetLastError());
+      }
       if (c->record_every > 0) {
         ch.mean = dalloc(gg.M * sizeof(double), &e);
         MG_CUDA(c, e);
@@ -1077,6 +1083,8 @@ mg_status create(mg_ctx** out, int32_t n_groups, const mg_grid* grids, const dou
   if (opt.record_every < 0) return fail(nullptr, MG_EINVAL, "record_every >= 0");
   if (opt.yz_cluster < 0) return fail(nullptr, MG_EINVAL, "yz_cluster >= 0");
   if (opt.mixing < 0 || opt.mixing > 2) return fail(nullptr, MG_EINVAL, "mixing must be 0, 1 or 2");
+  if (!(opt.start_dispersion >= 0.0) || !std::isfinite(opt.start_dispersion))
+    return fail(nullptr, MG_EINVAL, "start_dispersion must be finite and >= 0");
   if (opt.mixing && opt.fix_P) return fail(nullptr, MG_EINVAL, "mixing sweeps draw P; fix_P must be 0");
   if (opt.mixing && opt.persistent)
     return fail(nullptr, MG_EUNSUPPORTED, "mixing sweeps run one launch per pass (persistent must be 0)");
@@ -1168,6 +1176,7 @@ void mg_options_init(mg_options* o) {
   o->persistent = 0;
   o->autotune = 0;
   o->mixing = 0;
+  o->start_dispersion = 0.0;
 }
 
 mg_status mg_init(mg_ctx** out, const mg_grid* grid, const double* N, const double* R, const double* d,

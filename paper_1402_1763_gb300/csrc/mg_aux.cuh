@@ -303,6 +303,18 @@ __global__ void mixing_draw_kernel(const DrawDev* __restrict__ chains, int* stat
   }
 }
 
+// Over-dispersed start of one chain: P_b *= exp(sigma z_b), z_b the first
+// Box-Muller normal of Philox call (b, 0, chain, 2).
+__global__ void disperse_start_kernel(double* __restrict__ P, int B1, double sigma, uint32_t k0, uint32_t k1,
+                                      uint32_t cid) {
+  for (int b = threadIdx.x; b < B1; b += blockDim.x) {
+    const u32x4 w = philox4x32_10(uint32_t(b), 0u, cid, kStreamStart, k0, k1);
+    double z0, z1;
+    box_muller(w.x, w.y, z0, z1);
+    P[b] *= exp(sigma * z0);
+  }
+}
+
 // Advance the device sweep counter (end of a mixing sweep).
 __global__ void sweep_bump_kernel(uint32_t* sweep_ctr) { atomicAdd(sweep_ctr, 1u); }
 

@@ -106,6 +106,7 @@ __device__ __forceinline__ float radius2<float>(uint32_t w) {
 // Stream ids (counter word 3).
 constexpr uint32_t kStreamMessenger = 0;
 constexpr uint32_t kStreamModes = 1;
+constexpr uint32_t kStreamStart = 2;   // over-dispersed starting powers
 constexpr uint32_t kStreamMixing = 4;  // the mixing sweeps' per-shell proposals
 
 }  // namespace mg

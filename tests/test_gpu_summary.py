@@ -8,6 +8,8 @@ of the paper's efficiency analysis, posterior quantiles), through the C ABI.
   the trace read back (relative 1e-12; correlation lengths equal).
 * With record_every = 3 only every third sweep is recorded.
 * mg_pk_rhat over the chains against the oracle's Gelman-Rubin definition.
+* Over-dispersed starts (start_dispersion > 0): the starting P of every chain
+  and the chains after a few sweeps match the oracle.
 * Invalid lags and quantiles, and summaries without records, are MG_EINVAL.
 """
 import numpy as np
@@ -62,6 +64,23 @@ def test_rhat_across_chains(mixing):
         for burn in (0, 40):
             np.testing.assert_allclose(g.pk_rhat(0, 4, burn), summary.rhat(traces, burn), rtol=1e-12)
         np.testing.assert_allclose(g.pk_rhat(1, 2, 10), summary.rhat(traces[1:3], 10), rtol=1e-12)
+
+
+def test_over_dispersed_starts():
+    need_gpu()
+    from oracle import sampler as sp
+    from paper_1402_1763_gb300 import Sampler
+    from gpu_helpers import rel_l2
+    m = mockgen.make_mock(16, seed=6, n_bins=6, sigma_n=0.5)
+    prob = sp.make_problem(m.shape, m.L, m.N, m.R, m.d, 6)
+    orc = sp.Chains(prob, seed=9, chain_ids=[0, 1, 2], start_dispersion=1.5)
+    with Sampler.single(m.n, m.L, m.N, m.R, m.d, 6, 9, precision=64, n_chains=3, start_dispersion=1.5) as g:
+        for c in range(3):
+            np.testing.assert_allclose(g.read_pk(c), orc.P[c], rtol=1e-14)
+        orc.sweep(4)
+        g.sweep(4)
+        for c in range(3):
+            assert rel_l2(g.read_pk(c), orc.P[c]) <= 1e-12 and rel_l2(g.read_s(c), orc.s[c]) <= 1e-12
 
 
 def test_record_every_three():
