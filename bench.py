@@ -250,6 +250,49 @@ def run_other_workload(args):
         ms = ev[0].elapsed_time(ev[1]) / args.steps
         line.update(value=m.n ** 3 / (ms * 1e-3), ms_per_step=ms, dtype="f64",
                     config={"workload": w.name, "removed_fraction": m.removed_fraction})
+    elif args.workload == "precision-256":
+        # The precision form's accuracy as the 256^3 configuration states it:
+        # 16 FP32 chains over 2000 sweeps against the FP64 path (which matches
+        # the oracle to 1e-12) on the same seeds, chains 0 and 15, every 10th
+        # sweep: relative L2 of the mean s and mean P(k) over sweeps 21..2000
+        # and the worst single sweep.
+        w = mockgen.workload(3)
+        m = w.mocks[0]
+        S = 2000
+        mk = lambda prec, nc, c0: Sampler.single(m.n, m.L, m.N, m.R, m.d, m.n_bins, 3, precision=prec,
+                                                 n_chains=nc, chain_id0=c0, stream=stream.cuda_stream)
+        g32, g0, g15 = mk(32, 16, 0), mk(64, 1, 0), mk(64, 1, 15)
+        acc = {c: [0.0, 0.0, 0.0, 0.0] for c in (0, 15)}
+        worst_s = worst_p = 0.0
+        t0 = time.perf_counter()
+        for sw in range(1, S + 1):
+            g32.sweep(1)
+            g0.sweep(1)
+            g15.sweep(1)
+            if sw % 10:
+                continue
+            for c, g64 in ((0, g0), (15, g15)):
+                s32, s64 = g32.read_s(c).astype(np.float64), g64.read_s(0)
+                p32, p64 = g32.read_pk(c), g64.read_pk(0)
+                worst_s = max(worst_s, float(np.linalg.norm(s32 - s64) / np.linalg.norm(s64)))
+                worst_p = max(worst_p, float(np.linalg.norm(p32 - p64) / np.linalg.norm(p64)))
+                if sw > 20:
+                    a = acc[c]
+                    a[0], a[1], a[2], a[3] = a[0] + s32, a[1] + s64, a[2] + p32, a[3] + p64
+        dt = time.perf_counter() - t0
+        rel = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))
+        errs = {f"chain{c}_mean_s_rel_l2": rel(acc[c][0], acc[c][1]) for c in (0, 15)}
+        errs.update({f"chain{c}_mean_P_rel_l2": rel(acc[c][2], acc[c][3]) for c in (0, 15)})
+        g0.close()
+        g15.close()
+        g = g32
+        line.update(metric="FP32 precision form against the FP64 path, 2000 sweeps at 256^3: worst relative L2 "
+                           "of the mean s and mean P(k)",
+                    value=max(errs.values()), unit="relative L2", higher_is_better=False,
+                    ms_per_step=dt * 1e3 / S, dtype="f32",
+                    config={"workload": w.name + "-2000-sweeps", "chains_compared": [0, 15],
+                            "sampling": "every 10th sweep; means over sweeps 21..2000"},
+                    errors=errs, worst_sample_s_rel_l2=worst_s, worst_sample_P_rel_l2=worst_p)
     elif args.workload == "mixing-256":
         w = mockgen.workload(3)
         m = w.mocks[0]
@@ -320,7 +363,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="256-fp32-16chains",
                     choices=["256-fp32-16chains", "batch-48chains", "adjoint-128", "fp64-128holes",
-                             "mixing-256", "mixing-acf"])
+                             "mixing-256", "mixing-acf", "precision-256"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = replicas.rank_world()
