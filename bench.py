@@ -420,6 +420,7 @@ def main():
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     sweep_bytes = yz_bytes + x_bytes
     traffic = None
+    inst = None
     prof = os.path.join(ROOT, "profiles", "pass_traffic_256cubed_fp32_16chains.json")
     if os.path.exists(prof):
         with open(prof) as f:
@@ -427,6 +428,25 @@ def main():
         # counters only count for the kernel build they were taken on
         if tr.get("source_hash") == kernel_source_hash():
             traffic = tr["per_launch_bytes"].get(dom)
+            inst = tr.get("warp_instructions_per_launch")
+    # instruction issue, the limit both passes actually meet: the ncu warp
+    # instruction count of a launch (same kernel build) over the live launch
+    # time, against 4 schedulers x 152 SMs issuing one warp instruction per
+    # cycle at the maximum SM clock
+    issue = None
+    if inst:
+        sm_mhz = 2070.0  # GB300 maximum SM clock
+        pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(pp):
+            with open(pp) as f:
+                sm_mhz = float(json.load(f).get("sm_max_mhz", sm_mhz))
+        issue_peak = 4 * 152 * sm_mhz * 1e6 / 1e9  # G warp instructions / s
+        issue = {}
+        for name, (kms, _) in kern.items():
+            if name in inst:
+                ach = inst[name] / (kms * 1e-3) / 1e9
+                issue[name] = {"warp_instructions": inst[name], "achieved_ginst_s": ach, "peak_ginst_s": issue_peak,
+                               "frac": ach / issue_peak}
 
     # end to end through the public API with host buffers: each step sweeps
     # all chains and reads every chain's P(k) back to pinned host memory
@@ -506,6 +526,7 @@ def main():
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": dom_bytes},
+        "issue_roofline": issue,
         "sweep_roofline": {"algorithmic_bytes_per_step": sweep_bytes,
                            "achieved_gbs": sweep_bytes / (ms * 1e-3) / 1e9,
                            "frac": sweep_bytes / (ms * 1e-3) / 1e9 / peak},
