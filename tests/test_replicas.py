@@ -32,7 +32,7 @@ def _worker(rank, world, port, out):
 
 def test_two_gloo_ranks_agree_on_max_time_and_disjoint_chains():
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
     assert out[0] == (0, 2, 0, 0, 2.5)
