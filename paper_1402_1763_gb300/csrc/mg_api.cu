@@ -82,6 +82,10 @@ struct mg_ctx {
   long long sweeps = 0;
   mg_status sticky = MG_OK;
   std::string err;
+  // one stream per grid size beyond the first, so that the size classes'
+  // passes of a sweep run as parallel branches (fork and join by events)
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> aux_ev;  // [0] fork, [1 + k] join of class k
   cudaGraphExec_t graph = nullptr;      // one plain sweep
   cudaGraphExec_t graph_mix = nullptr;  // one mixing sweep
   bool graph_failed = false;
@@ -312,11 +316,81 @@ mg_status launch_shell_draw(mg_ctx* c, int draw, bool count_sweep) {
   return MG_OK;
 }
 
+// Run fn(size class, stream) for every size class: in order on the context's
+// stream for one class, else as parallel branches forked from and joined
+// back into it (in a captured sweep they become parallel graph branches).
+template <typename F>
+mg_status for_each_class(mg_ctx* c, F fn) {
+  if (c->classes.size() < 2) {
+    for (auto& sc : c->classes) {
+      mg_status st = fn(sc, c->stream);
+      if (st != MG_OK) return st;
+    }
+    return MG_OK;
+  }
+  const size_t K = c->classes.size();
+  while (c->aux.size() < K) {
+    cudaStream_t st;
+    MG_CUDA(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    c->aux.push_back(st);
+  }
+  while (c->aux_ev.size() < K + 1) {
+    cudaEvent_t ev;
+    MG_CUDA(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    c->aux_ev.push_back(ev);
+  }
+  MG_CUDA(c, cudaEventRecord(c->aux_ev[0], c->stream));
+  for (size_t k = 0; k < K; ++k) {
+    MG_CUDA(c, cudaStreamWaitEvent(c->aux[k], c->aux_ev[0], 0));
+    mg_status st = fn(c->classes[k], c->aux[k]);
+    if (st != MG_OK) return st;
+    MG_CUDA(c, cudaEventRecord(c->aux_ev[1 + k], c->aux[k]));
+  }
+  for (size_t k = 0; k < K; ++k) MG_CUDA(c, cudaStreamWaitEvent(c->stream, c->aux_ev[1 + k], 0));
+  return MG_OK;
+}
+
 // which: bit 1 = pass YZ of every size class, bit 2 = pass X, bit 4 = shell draw.
+// A whole sweep (which = 7) runs each size class's passes as its own branch.
 template <typename T>
 mg_status enqueue_passes(mg_ctx* c, int which, bool mix) {
-  const uint32_t* sw = static_cast<const uint32_t*>(c->d_sweep->p);
-  (void)sw;
+  auto yz = [c](SizeClass& sc, cudaStream_t st) -> mg_status {
+    for (auto& blob : sc.args)
+      MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, 0, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()), st));
+    return MG_OK;
+  };
+  auto xpass = [c](int mode) {
+    return [c, mode](SizeClass& sc, cudaStream_t st) -> mg_status {
+      for (auto& blob : sc.args)
+        MG_CUDA(c, launch_pass_x<T>(sc.n, mode, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()), sc.B_max, st));
+      return MG_OK;
+    };
+  };
+  if (which == 7) {
+    mg_status st;
+    if (mix) {
+      auto first = [&](SizeClass& sc, cudaStream_t s) -> mg_status {
+        mg_status r = yz(sc, s);
+        return r != MG_OK ? r : xpass(kXMixDraw)(sc, s);
+      };
+      if ((st = for_each_class(c, first)) != MG_OK) return st;
+      const dim3 grid(unsigned(c->chains.size()), unsigned(c->B_max + 1));
+      mixing_draw_kernel<T><<<grid, 256, 0, c->stream>>>(static_cast<const DrawDev*>(c->d_draw->p),
+                                                         static_cast<int*>(c->d_status->p),
+                                                         static_cast<const uint32_t*>(c->d_sweep->p));
+      MG_CUDA(c, cudaGetLastError());
+      if ((st = for_each_class(c, xpass(kXMixScale))) != MG_OK) return st;
+      sweep_bump_kernel<<<1, 1, 0, c->stream>>>(static_cast<uint32_t*>(c->d_sweep->p));
+      MG_CUDA(c, cudaGetLastError());
+      return MG_OK;
+    }
+    auto both = [&](SizeClass& sc, cudaStream_t s) -> mg_status {
+      mg_status r = yz(sc, s);
+      return r != MG_OK ? r : xpass(0)(sc, s);
+    };
+    if ((st = for_each_class(c, both)) != MG_OK) return st;
+    return launch_shell_draw<T>(c, 1, true);
+  }
   if (which & 1) {
     for (auto& sc : c->classes)
       for (auto& blob : sc.args)
@@ -1574,6 +1648,11 @@ void mg_destroy(mg_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->graph_mix) cudaGraphExecDestroy(c->graph_mix);
+  for (cudaStream_t st : c->aux) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  for (cudaEvent_t ev : c->aux_ev) cudaEventDestroy(ev);
   c->classes.clear();
   c->chains.clear();
   c->groups.clear();
