@@ -10,6 +10,8 @@ waits of the persistent kernel.
 * The tuner leaves the chains untouched and picks a valid schedule.
 * A wait budget of one cycle makes the x tiles give up on their y/z planes:
   the device reports MG_ETIMEOUT (sticky) and nothing faults or hangs.
+* 70 chains on one data set (more than one launch holds) match the oracle on
+  both sides of the split.
 """
 import numpy as np
 import pytest
@@ -111,3 +113,20 @@ def test_wait_budget_exhaustion_is_reported():
         assert e2.value.status == MG_ETIMEOUT
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_more_chains_than_one_launch_holds(precision):
+    """70 chains of one data set: the passes are issued in launches of at most
+    64 chains each; chains on both sides of the split match the oracle."""
+    need_gpu()
+    from gpu_helpers import gpu_sampler
+    m = mockgen.make_mock(16, seed=70, n_bins=4)
+    follow = [0, 63, 64, 69]
+    orc = oracle_chains(m, 4, 31, follow)
+    orc.sweep(2)
+    with gpu_sampler(m, 4, 31, precision, n_chains=70) as g:
+        g.sweep(2)
+        for k, c in enumerate(follow):
+            assert rel_l2(g.read_s(c), orc.s[k]) <= TOL[precision]
+            assert rel_l2(g.read_pk(c), orc.P[k]) <= TOL[precision]
