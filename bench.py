@@ -454,15 +454,14 @@ def main():
 
     # end to end through the public API with host buffers: each step sweeps
     # all chains and reads every chain's P(k) back to pinned host memory
-    from paper_1402_1763_gb300 import mg_read_pk
-    pk = [torch.empty(N_BINS + 1, dtype=torch.float64, pin_memory=True).numpy() for _ in range(N_CHAINS)]
+    from paper_1402_1763_gb300 import mg_read_pk_all
+    pk = torch.empty((N_CHAINS, N_BINS + 1), dtype=torch.float64, pin_memory=True).numpy()
     smp.sync()
     replicas.barrier(dd)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         smp.sweep(1)
-        for c in range(N_CHAINS):
-            mg_read_pk(smp.ctx, c, pk[c])
+        mg_read_pk_all(smp.ctx, pk)
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_s = replicas.max_over_ranks(e2e_s, dd)
     smp.close()

@@ -174,6 +174,13 @@ mg_status mg_read_s(mg_ctx* ctx, int32_t chain, void* out, int32_t out_is_device
  * overflow shell.  Synchronises. */
 mg_status mg_read_pk(mg_ctx* ctx, int32_t chain, double* out);
 
+/* Current P of every chain in one transfer: out (host, ideally pinned) gets
+ * n_chains rows of B_max+1 doubles, B_max the largest n_bins in the context;
+ * row c holds chain c's n_bins+1 values, the rest of the row is 0.  One copy
+ * and one synchronisation for the whole batch (a per-sweep read of all chains
+ * costs about as much as one mg_read_pk).  Synchronises. */
+mg_status mg_read_pk_all(mg_ctx* ctx, double* out);
+
 /* Statistics of one chain (see mg_stats). Synchronises. */
 mg_status mg_read_stats(mg_ctx* ctx, int32_t chain, mg_stats* out);
 

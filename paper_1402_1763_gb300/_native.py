@@ -91,6 +91,7 @@ def library():
         "mg_pk_acf": (C.c_int, [_P, C.c_int32, C.c_int32, _D, C.POINTER(C.c_int32)]),
         "mg_pk_quantiles": (C.c_int, [_P, C.c_int32, C.c_int32, _D, _D]),
         "mg_pk_rhat": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int64, _D]),
+        "mg_read_pk_all": (C.c_int, [_P, _D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -214,6 +215,11 @@ def mg_pk_quantiles(ctx, chain: int, q: np.ndarray, out: np.ndarray):
 
 def mg_pk_rhat(ctx, first_chain: int, n_chains: int, burn: int, out: np.ndarray):
     _check(library().mg_pk_rhat(ctx, int(first_chain), int(n_chains), int(burn), _dptr(out)), ctx)
+
+
+def mg_read_pk_all(ctx, out: np.ndarray):
+    """out: (n_chains, B_max+1) float64, C-contiguous (pinned host memory for speed)."""
+    _check(library().mg_read_pk_all(ctx, _dptr(out)), ctx)
 
 
 def mg_read_stats(ctx, chain: int, stats: MgStats):
@@ -415,6 +421,15 @@ class Sampler:
         nb = self.info(chain)[1]
         out = np.empty(nb + 1)
         mg_read_pk(self.ctx, chain, out)
+        return out
+
+    def read_pk_all(self, out=None) -> np.ndarray:
+        """Every chain's P(k) in one transfer, shape (n_chains, max n_bins + 1);
+        a chain with fewer shells is padded with zeros."""
+        if out is None:
+            B1 = max(self.info(c)[1] for c in range(self.n_chains)) + 1
+            out = np.empty((self.n_chains, B1))
+        mg_read_pk_all(self.ctx, out)
         return out
 
     def read_stats(self, chain=0, fields=True, maps=False) -> dict:

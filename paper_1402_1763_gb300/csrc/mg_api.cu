@@ -78,6 +78,7 @@ struct mg_ctx {
   std::vector<SizeClass> classes;
   std::shared_ptr<DevBuf> d_draw;  // DrawDev[chains]
   std::shared_ptr<DevBuf> d_sweep, d_status, d_scratch_s;
+  std::shared_ptr<DevBuf> d_pk_all;  // staging of mg_read_pk_all
   int B_max = 0;
   long long sweeps = 0;
   mg_status sticky = MG_OK;
@@ -1376,6 +1377,23 @@ mg_status mg_read_pk(mg_ctx* c, int32_t chain, double* out) {
   return check_status(c);
 }
 
+mg_status mg_read_pk_all(mg_ctx* c, double* out) {
+  if (!c || !out) return MG_EINVAL;
+  const int B1 = c->B_max + 1;
+  const size_t bytes = c->chains.size() * size_t(B1) * sizeof(double);
+  if (!c->d_pk_all) {
+    cudaError_t e;
+    c->d_pk_all = dalloc(bytes, &e);
+    MG_CUDA(c, e);
+  }
+  gather_pk_kernel<<<unsigned(c->chains.size()), 128, 0, c->stream>>>(static_cast<const DrawDev*>(c->d_draw->p), B1,
+                                                                     static_cast<double*>(c->d_pk_all->p));
+  MG_CUDA(c, cudaGetLastError());
+  MG_CUDA(c, cudaMemcpyAsync(out, c->d_pk_all->p, bytes, cudaMemcpyDeviceToHost, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
 mg_status mg_read_stats(mg_ctx* c, int32_t chain, mg_stats* out) {
   if (!c || !out) return MG_EINVAL;
   if (!valid_chain(c, chain)) return fail(c, MG_EINVAL, "chain index out of range");
@@ -1657,6 +1675,7 @@ void mg_destroy(mg_ctx* c) {
   c->chains.clear();
   c->groups.clear();
   c->d_draw.reset();
+  c->d_pk_all.reset();
   c->d_sweep.reset();
   c->d_status.reset();
   c->d_scratch_s.reset();

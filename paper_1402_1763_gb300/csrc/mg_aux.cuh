@@ -315,6 +315,14 @@ __global__ void disperse_start_kernel(double* __restrict__ P, int B1, double sig
   }
 }
 
+// Every chain's P into one row-major staging array of B_max+1 columns (zero
+// padded).  Grid: chains.
+__global__ void gather_pk_kernel(const DrawDev* __restrict__ chains, int B1max, double* __restrict__ out) {
+  const DrawDev cd = chains[blockIdx.x];
+  for (int b = threadIdx.x; b < B1max; b += blockDim.x)
+    out[size_t(blockIdx.x) * B1max + b] = b <= cd.B ? cd.P[b] : 0.0;
+}
+
 // Advance the device sweep counter (end of a mixing sweep).
 __global__ void sweep_bump_kernel(uint32_t* sweep_ctr) { atomicAdd(sweep_ctr, 1u); }
 

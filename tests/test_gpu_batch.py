@@ -12,6 +12,8 @@ waits of the persistent kernel.
   the device reports MG_ETIMEOUT (sticky) and nothing faults or hangs.
 * 70 chains on one data set (more than one launch holds) match the oracle on
   both sides of the split.
+* mg_read_pk_all returns every chain's P(k) in one transfer, equal to the
+  per-chain reads, with zero padding for the chains with fewer shells.
 """
 import numpy as np
 import pytest
@@ -130,3 +132,21 @@ def test_more_chains_than_one_launch_holds(precision):
         for k, c in enumerate(follow):
             assert rel_l2(g.read_s(c), orc.s[k]) <= TOL[precision]
             assert rel_l2(g.read_pk(c), orc.P[k]) <= TOL[precision]
+
+
+def test_read_pk_all_matches_per_chain_reads():
+    need_gpu()
+    mocks, seeds = mixed()
+    with batch(mocks, seeds, 32, n_chains=2) as g:
+        g.sweep(3)
+        allp = g.read_pk_all()
+        B1 = max(m.n_bins for m in mocks) + 1
+        assert allp.shape == (6, B1)
+        for c in range(6):
+            p = g.read_pk(c)
+            np.testing.assert_array_equal(allp[c, :p.size], p)
+            assert np.all(allp[c, p.size:] == 0.0)
+        g.sweep(1)
+        again = np.full((6, B1), np.nan)
+        g.read_pk_all(again)
+        assert np.array_equal(again[0, :5], g.read_pk(0)) and not np.array_equal(again, allp)
