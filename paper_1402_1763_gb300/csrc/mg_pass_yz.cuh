@@ -133,14 +133,38 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
   const uint32_t sweep = *a.sweep_ctr;
   const T tau = cd.tau;
 
-  if constexpr (C > 1) cluster_barrier<C>();  // every CTA of the cluster is running
+  // Every CTA of the cluster must be running before another writes into its
+  // shared memory.  The arrive needs no ordering; the wait comes after this
+  // thread's first global loads of stage I1 are in flight.
+  if constexpr (C > 1) {
+    if constexpr (MODE == kModeLoad) cluster_barrier<C>();
+    else asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory");
+  }
 
   if constexpr (MODE != kModeLoad) {
+    // Prefetch into L2 the rows that stage I1 of this CTA will read for the
+    // unit pf_units ahead in launch order (the one expected to take this
+    // cluster's place), so its loads hit L2 rather than HBM.
+    {
+      const int un = unit + a.pf_units;
+      if (a.pf_units > 0 && un < N * a.n_chains) {
+        const V2* nmain = a.chains[un % a.n_chains].main + size_t(un / a.n_chains) * N * H;
+        constexpr int kLines = (H * int(sizeof(V2)) + 127) / 128;
+        for (int i = threadIdx.x; i < P * QC * kLines; i += NT) {
+          const int rw = i / kLines, ln = i % kLines;
+          const int u = rw / QC, v = int(rank) * QC + rw % QC;
+          const char* pa = reinterpret_cast<const char*>(nmain + size_t(Q * u + v) * H) + ln * 128;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+        }
+      }
+    }
+
     // Column stage I1 (per v of this CTA): IDFT_P over u of X[Q u + v] from
     // global, twiddle W_N^{-p v}, to slot p*Q + v (whichever CTA owns it).
     // A thread issues the loads of BI items before transforming any of them.
     constexpr int TI1 = H * QC;
     constexpr int BI = TI1 >= 2 * NT ? 2 : 1;
+    bool start_wait = C > 1;  // the start barrier's wait is still due
     for (int it0 = threadIdx.x; it0 < TI1; it0 += BI * NT) {
       cx<T> X[BI][P];
 #pragma unroll
@@ -158,6 +182,12 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
               X[b][u] = {X[b][u].re - y.im, X[b][u].im + y.re};
             }
           }
+        }
+      }
+      if constexpr (C > 1) {
+        if (start_wait) {
+          cluster_wait<C>();
+          start_wait = false;
         }
       }
 #pragma unroll
@@ -178,6 +208,9 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
           else st_dsmem(rbase[p / PC] + uint32_t(off) * kEl, y);
         }
       }
+    }
+    if constexpr (C > 1) {
+      if (start_wait) cluster_wait<C>();
     }
     cluster_barrier<C>();
 

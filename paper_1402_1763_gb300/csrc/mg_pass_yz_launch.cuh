@@ -18,8 +18,19 @@ constexpr int yz_threads() {
   return N < 48 ? 128 : (yz_minblocks<T, N, C>() == 2 ? 256 : 512);
 }
 
+inline int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
 template <typename T, int N, int C, int MODE>
-cudaError_t run(const LaunchArgs<T>& args, cudaStream_t st) {
+cudaError_t run(const LaunchArgs<T>& args_in, cudaStream_t st) {
+  // Clusters are started in launch order as earlier ones finish, so the unit
+  // one resident-cluster count ahead is the one that takes a cluster's place.
+  LaunchArgs<T> args = args_in;
+  args.pf_units = sm_count() * yz_minblocks<T, N, C>() / C;
   const int n_chains = args.n_chains;
   constexpr int NT = yz_threads<T, N, C>();
   using S = PassYZShape<T, N, C>;
