@@ -15,6 +15,16 @@ bool supported_n(int n);
 int yz_cluster_choices(int n, int precision, int* out, int max_out);
 size_t yz_smem_bytes(int n, int C, int precision);
 
+// Multiprocessors of the current device (0 if the query fails): with the
+// resident CTAs per SM it gives how far ahead in launch order the CTA that
+// takes a finishing CTA's place lies (the passes prefetch its input into L2).
+inline int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
 // n_chains == 0 only sets the kernels' attributes (done once, outside any
 // stream capture).
 template <typename T>

@@ -18,8 +18,8 @@ constexpr int pass_x_minblocks() {
 }
 
 template <typename T, int N, int MODE>
-cudaError_t run_x(const LaunchArgs<T>& args, int B_max, cudaStream_t st) {
-  const int n_chains = args.n_chains;
+cudaError_t run_x(const LaunchArgs<T>& args_in, int B_max, cudaStream_t st) {
+  const int n_chains = args_in.n_chains;
   constexpr int NT = pass_x_threads<N>();
   using S = PassXShape<T, N>;
   constexpr bool adj = MODE == kXAdjTop || MODE == kXAdjMid;
@@ -27,6 +27,8 @@ cudaError_t run_x(const LaunchArgs<T>& args, int B_max, cudaStream_t st) {
   auto kern = pass_x_kernel<T, N, NT, adj ? 1 : pass_x_minblocks<T, N>(), MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess || n_chains == 0) return e;  // n_chains == 0: set attributes only
+  LaunchArgs<T> args = args_in;
+  args.pf_units = sm_count() * (adj ? 1 : pass_x_minblocks<T, N>());
   const unsigned grid = unsigned(S::kTiles) * unsigned(n_chains);
   kern<<<grid, NT, smem, st>>>(args);
   return cudaGetLastError();

@@ -318,6 +318,27 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
     base2 = (nyq_tile ? cd.nyq2 : cd.main2) + off;
   }
 
+  // Prefetch into L2 the pencils of the tile pf_units ahead in launch order
+  // (the one expected to take this CTA's place), so its stage F1 loads hit
+  // L2 rather than HBM.  Main tiles only; lines that start past the last
+  // pencil are skipped.
+  if constexpr (!kAdj && !kMixScale) {
+    const int nb = block + a.pf_units;
+    if (a.pf_units > 0 && nb < S::kTiles * a.n_chains && nb % S::kTiles < S::kMainTiles) {
+      const int f0 = (nb % S::kTiles) * LW;
+      const V2* nbase = a.chains[nb / S::kTiles].main + f0;
+      constexpr int kPerLine = 128 / int(sizeof(V2));
+      constexpr int kLines = (LW + kPerLine - 1) / kPerLine;
+      for (int i = threadIdx.x; i < N * kLines; i += NT) {
+        const int kx = i / kLines, ln = i % kLines;
+        if (f0 + ln * kPerLine < N * H) {
+          const V2* pa = nbase + size_t(kx) * N * H + ln * kPerLine;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
+        }
+      }
+    }
+  }
+
   // Mixing sweep, second half: the modes (kx = slot index) come back from k
   // space; the column loop below scales them and runs the inverse stage I1.
   if constexpr (kMixScale) {

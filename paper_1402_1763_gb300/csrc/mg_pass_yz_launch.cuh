@@ -18,13 +18,6 @@ constexpr int yz_threads() {
   return N < 48 ? 128 : (yz_minblocks<T, N, C>() == 2 ? 256 : 512);
 }
 
-inline int sm_count() {
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  return sms;
-}
-
 template <typename T, int N, int C, int MODE>
 cudaError_t run(const LaunchArgs<T>& args_in, cudaStream_t st) {
   // Clusters are started in launch order as earlier ones finish, so the unit
