@@ -96,7 +96,7 @@ struct LaunchArgs {
   const uint32_t* sweep_ctr;
   const typename VT<T>::c2* tw;  // twiddle tables of this grid size (TwLayout)
   int n_chains;
-  int pf_units;  // pass YZ: prefetch into L2 the input of unit + pf_units (0: none)
+  int pf_units;  // pass X: prefetch into L2 the input of tile + pf_units (0: none)
   uint32_t k0[kMaxLaunchChains];
   uint32_t k1[kMaxLaunchChains];
   uint32_t cid[kMaxLaunchChains];

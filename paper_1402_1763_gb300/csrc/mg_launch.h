@@ -15,9 +15,8 @@ bool supported_n(int n);
 int yz_cluster_choices(int n, int precision, int* out, int max_out);
 size_t yz_smem_bytes(int n, int C, int precision);
 
-// Multiprocessors of the current device (0 if the query fails): with the
-// resident CTAs per SM it gives how far ahead in launch order the CTA that
-// takes a finishing CTA's place lies (the passes prefetch its input into L2).
+// Multiprocessors of the current device (0 if the query fails): how far
+// ahead in launch order pass X prefetches a tile's input into L2.
 inline int sm_count() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;

@@ -319,9 +319,9 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
   }
 
   // Prefetch into L2 the pencils of the tile pf_units ahead in launch order
-  // (the one expected to take this CTA's place), so its stage F1 loads hit
-  // L2 rather than HBM.  Main tiles only; lines that start past the last
-  // pencil are skipped.
+  // (CTAs start in launch order as earlier ones finish, so it starts soon),
+  // so its stage F1 loads hit L2 rather than HBM.  Main tiles only; lines
+  // that start past the last pencil are skipped.
   if constexpr (!kAdj && !kMixScale) {
     const int nb = block + a.pf_units;
     if (a.pf_units > 0 && nb < S::kTiles * a.n_chains && nb % S::kTiles < S::kMainTiles) {

@@ -142,23 +142,6 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
   }
 
   if constexpr (MODE != kModeLoad) {
-    // Prefetch into L2 the rows that stage I1 of this CTA will read for the
-    // unit pf_units ahead in launch order (the one expected to take this
-    // cluster's place), so its loads hit L2 rather than HBM.
-    {
-      const int un = unit + a.pf_units;
-      if (a.pf_units > 0 && un < N * a.n_chains) {
-        const V2* nmain = a.chains[un % a.n_chains].main + size_t(un / a.n_chains) * N * H;
-        constexpr int kLines = (H * int(sizeof(V2)) + 127) / 128;
-        for (int i = threadIdx.x; i < P * QC * kLines; i += NT) {
-          const int rw = i / kLines, ln = i % kLines;
-          const int u = rw / QC, v = int(rank) * QC + rw % QC;
-          const char* pa = reinterpret_cast<const char*>(nmain + size_t(Q * u + v) * H) + ln * 128;
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
-        }
-      }
-    }
-
     // Column stage I1 (per v of this CTA): IDFT_P over u of X[Q u + v] from
     // global, twiddle W_N^{-p v}, to slot p*Q + v (whichever CTA owns it).
     // A thread issues the loads of BI items before transforming any of them.

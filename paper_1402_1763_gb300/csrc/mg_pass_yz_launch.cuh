@@ -19,11 +19,7 @@ constexpr int yz_threads() {
 }
 
 template <typename T, int N, int C, int MODE>
-cudaError_t run(const LaunchArgs<T>& args_in, cudaStream_t st) {
-  // Clusters are started in launch order as earlier ones finish, so the unit
-  // one resident-cluster count ahead is the one that takes a cluster's place.
-  LaunchArgs<T> args = args_in;
-  args.pf_units = sm_count() * yz_minblocks<T, N, C>() / C;
+cudaError_t run(const LaunchArgs<T>& args, cudaStream_t st) {
   const int n_chains = args.n_chains;
   constexpr int NT = yz_threads<T, N, C>();
   using S = PassYZShape<T, N, C>;
