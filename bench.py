@@ -240,7 +240,7 @@ def run_other_workload(args):
         line.update(metric="adjoint of K = 8 fixed-P sweeps (loss + dL/dlogP + dL/dd), wall time",
                     value=dt * 1e3, unit="ms per call", higher_is_better=False, ms_per_step=dt * 1e3,
                     dtype="f32", config={"workload": w.name, "K": 8,
-                                         "note": "host buffers in and out; includes per-call allocations"})
+                                         "note": "host buffers in and out (weights, dL/dd); work buffers kept between calls"})
     elif args.workload == "fp64-128holes":
         w = mockgen.workload(2)
         m = w.mocks[0]

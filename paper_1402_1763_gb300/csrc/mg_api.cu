@@ -48,6 +48,7 @@ struct Chain {
   int group = 0;
   uint32_t chain_id = 0;
   std::shared_ptr<DevBuf> main, nyq, coef, mscale, partial, P, sig, chi, mean, m2;
+  std::shared_ptr<DevBuf> rec_desc;  // the chain's descriptor with the scratch field as output
   std::shared_ptr<DevBuf> trace;  // [records][B+1] P after every record_every-th sweep
   long long trace_cap = 0;        // records the trace buffer holds
 };
@@ -59,8 +60,16 @@ struct SizeClass {
   int B_max = 0;
   std::vector<int> chains;         // context chain indices
   std::shared_ptr<DevBuf> d_desc;  // ChainDev<T>[chains.size()]
+  std::vector<char> h_desc;        // host copy of d_desc
   std::shared_ptr<DevBuf> tw;      // twiddle tables (TwLayout), context precision
   std::vector<std::vector<char>> args;  // LaunchArgs<T> per chunk of <= kMaxLaunchChains chains
+};
+
+// Work buffers of mg_adjoint for one grid size, kept between calls.
+struct AdjWork {
+  int K_cap = 0;  // checkpoints ck holds
+  int B1 = 0;     // shells + 1 that acc and Psave hold
+  std::shared_ptr<DevBuf> ck, scr, adj, wl64, wl, dd, ddw, acc, Psave, desc, sw;
 };
 
 }  // namespace
@@ -79,6 +88,7 @@ struct mg_ctx {
   std::shared_ptr<DevBuf> d_draw;  // DrawDev[chains]
   std::shared_ptr<DevBuf> d_sweep, d_status, d_scratch_s;
   std::shared_ptr<DevBuf> d_pk_all;  // staging of mg_read_pk_all
+  std::map<int, AdjWork> adj_work;   // mg_adjoint's buffers per grid size
   int B_max = 0;
   long long sweeps = 0;
   mg_status sticky = MG_OK;
@@ -241,7 +251,6 @@ mg_status upload_descriptors(mg_ctx* c) {
       ChainDev<T>& d = h[i];
       d.main = static_cast<V2*>(ch.main->p);
       d.nyq = static_cast<V2*>(ch.nyq->p);
-      d.bc = static_cast<const V2*>(g.bc->p);
       d.row_info = static_cast<const uint2*>(g.row_info->p);
       d.bc_rows = static_cast<const V2*>(g.bc_rows->p);
       d.coef = static_cast<const V2*>(ch.coef->p);
@@ -257,6 +266,7 @@ mg_status upload_descriptors(mg_ctx* c) {
     sc.d_desc = dalloc(h.size() * sizeof(ChainDev<T>), &e);
     MG_CUDA(c, e);
     MG_CUDA(c, cudaMemcpy(sc.d_desc->p, h.data(), h.size() * sizeof(ChainDev<T>), cudaMemcpyHostToDevice));
+    sc.h_desc.assign(reinterpret_cast<const char*>(h.data()), reinterpret_cast<const char*>(h.data() + h.size()));
     const auto tw = twiddles<T>(sc.n);
     sc.tw = dalloc(tw.size() * sizeof(V2), &e);
     MG_CUDA(c, e);
@@ -648,36 +658,53 @@ mg_status tune_impl(mg_ctx* c, int reps) {
   return check_status(c);
 }
 
-// Launch arguments for one chain with an input or output field pointer attached.
+// The size class of a chain and its index there (false if out of range).
+bool find_chain(mg_ctx* c, int chain, SizeClass** sc, size_t* idx) {
+  for (auto& k : c->classes)
+    for (size_t i = 0; i < k.chains.size(); ++i)
+      if (k.chains[i] == chain) {
+        *sc = &k;
+        *idx = i;
+        return true;
+      }
+  return false;
+}
+
+// Launch arguments of one chain (n_chains = 1) with the descriptor `dev`.
+template <typename T>
+LaunchArgs<T> one_chain_args(const SizeClass& sc, size_t i, const ChainDev<T>* dev) {
+  const LaunchArgs<T>& src = *reinterpret_cast<const LaunchArgs<T>*>(sc.args[i / kMaxLaunchChains].data());
+  LaunchArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.chains = dev;
+  a.sweep_ctr = src.sweep_ctr;
+  a.tw = src.tw;
+  a.n_chains = 1;
+  a.k0[0] = src.k0[i % kMaxLaunchChains];
+  a.k1[0] = src.k1[i % kMaxLaunchChains];
+  a.cid[0] = src.cid[i % kMaxLaunchChains];
+  return a;
+}
+
+// Launch arguments for one chain with an input or output field pointer
+// attached (a descriptor of its own in *desc).
 template <typename T>
 mg_status single_chain_args(mg_ctx* c, int chain, T* s_out, const T* s_in, SizeClass** sc_out,
                             std::shared_ptr<DevBuf>* desc, LaunchArgs<T>* args) {
-  for (auto& sc : c->classes) {
-    for (size_t i = 0; i < sc.chains.size(); ++i) {
-      if (sc.chains[i] != chain) continue;
-      ChainDev<T> h;
-      MG_CUDA(c, cudaMemcpy(&h, static_cast<ChainDev<T>*>(sc.d_desc->p) + i, sizeof(h), cudaMemcpyDeviceToHost));
-      h.s_out = s_out;
-      h.s_in = s_in;
-      cudaError_t e;
-      *desc = dalloc(sizeof(h), &e);
-      MG_CUDA(c, e);
-      MG_CUDA(c, cudaMemcpyAsync((*desc)->p, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
-      MG_CUDA(c, cudaStreamSynchronize(c->stream));
-      const LaunchArgs<T>& src = *reinterpret_cast<const LaunchArgs<T>*>(sc.args[i / kMaxLaunchChains].data());
-      std::memset(args, 0, sizeof(*args));
-      args->chains = static_cast<const ChainDev<T>*>((*desc)->p);
-      args->sweep_ctr = src.sweep_ctr;
-      args->tw = src.tw;
-      args->n_chains = 1;
-      args->k0[0] = src.k0[i % kMaxLaunchChains];
-      args->k1[0] = src.k1[i % kMaxLaunchChains];
-      args->cid[0] = src.cid[i % kMaxLaunchChains];
-      *sc_out = &sc;
-      return MG_OK;
-    }
-  }
-  return fail(c, MG_EINVAL, "chain index out of range");
+  SizeClass* sc;
+  size_t i;
+  if (!find_chain(c, chain, &sc, &i)) return fail(c, MG_EINVAL, "chain index out of range");
+  ChainDev<T> h = reinterpret_cast<const ChainDev<T>*>(sc->h_desc.data())[i];
+  h.s_out = s_out;
+  h.s_in = s_in;
+  cudaError_t e;
+  *desc = dalloc(sizeof(h), &e);
+  MG_CUDA(c, e);
+  MG_CUDA(c, cudaMemcpyAsync((*desc)->p, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+  MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  *args = one_chain_args<T>(*sc, i, static_cast<const ChainDev<T>*>((*desc)->p));
+  *sc_out = sc;
+  return MG_OK;
 }
 
 template <typename T>
@@ -712,24 +739,6 @@ mg_status load_s(mg_ctx* c, int chain, const T* in_dev) {
 // ---------------------------------------------------------------------------
 
 template <typename T>
-mg_status upload_desc(mg_ctx* c, const ChainDev<T>& h, std::shared_ptr<DevBuf>* buf, LaunchArgs<T>* a) {
-  cudaError_t e;
-  *buf = dalloc(sizeof(h), &e);
-  MG_CUDA(c, e);
-  MG_CUDA(c, cudaMemcpyAsync((*buf)->p, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
-  MG_CUDA(c, cudaStreamSynchronize(c->stream));
-  a->chains = static_cast<const ChainDev<T>*>((*buf)->p);
-  return MG_OK;
-}
-
-template <typename T>
-mg_status set_sweep_ctr(mg_ctx* c, uint32_t v) {
-  MG_CUDA(c, cudaMemcpyAsync(c->d_sweep->p, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream));
-  MG_CUDA(c, cudaStreamSynchronize(c->stream));
-  return MG_OK;
-}
-
-template <typename T>
 mg_status adjoint_impl(mg_ctx* c, int chain, int K, const double* logP, const double* wl_host, double* loss_out,
                        double* dlogP, double* dd_out) {
   using V2 = typename VT<T>::c2;
@@ -739,80 +748,112 @@ mg_status adjoint_impl(mg_ctx* c, int chain, int K, const double* logP, const do
   const size_t Mh = size_t(n) * n * (H + 1);
   const size_t main_b = size_t(n) * n * H * sizeof(V2), nyq_b = size_t(n) * n * sizeof(V2);
   const size_t state_b = main_b + nyq_b;
+  // the chain's size class, its descriptor and launch arguments
   SizeClass* sc;
-  std::shared_ptr<DevBuf> d0;
-  LaunchArgs<T> base;
-  mg_status st = single_chain_args<T>(c, chain, nullptr, nullptr, &sc, &d0, &base);
-  if (st != MG_OK) return st;
-  ChainDev<T> cd0;
-  MG_CUDA(c, cudaMemcpy(&cd0, base.chains, sizeof(cd0), cudaMemcpyDeviceToHost));
+  size_t ci;
+  if (!find_chain(c, chain, &sc, &ci)) return fail(c, MG_EINVAL, "chain index out of range");
+  const ChainDev<T> cd0 = reinterpret_cast<const ChainDev<T>*>(sc->h_desc.data())[ci];
+  LaunchArgs<T> base = one_chain_args<T>(*sc, ci, static_cast<const ChainDev<T>*>(sc->d_desc->p) + ci);
+
+  // work buffers, kept between calls for this grid size
+  AdjWork& w = c->adj_work[n];
   cudaError_t e;
-  auto ck = dalloc(state_b * size_t(K + 1), &e);
-  MG_CUDA(c, e);
-  auto scr = dalloc(state_b, &e);
-  MG_CUDA(c, e);
-  auto adj = dalloc(state_b, &e);
-  MG_CUDA(c, e);
-  auto wl = dalloc(Mh * sizeof(T), &e);
-  MG_CUDA(c, e);
-  auto dd = dalloc(g.M * sizeof(T), &e);
-  MG_CUDA(c, e);
-  auto acc = dalloc(size_t(2) * B1 * sizeof(double), &e);
-  MG_CUDA(c, e);
-  auto Psave = dalloc(size_t(B1) * sizeof(double), &e);
-  MG_CUDA(c, e);
-  auto ddw = dalloc(g.M * sizeof(double), &e);
-  MG_CUDA(c, e);
-  {
+  if (!w.scr) {
+    w.scr = dalloc(state_b, &e);
+    MG_CUDA(c, e);
+    w.adj = dalloc(state_b, &e);
+    MG_CUDA(c, e);
+    w.wl64 = dalloc(Mh * sizeof(double), &e);
+    MG_CUDA(c, e);
+    w.wl = dalloc(Mh * sizeof(T), &e);
+    MG_CUDA(c, e);
+    w.dd = dalloc(g.M * sizeof(T), &e);
+    MG_CUDA(c, e);
+    w.ddw = dalloc(g.M * sizeof(double), &e);
+    MG_CUDA(c, e);
+    w.desc = dalloc(5 * sizeof(ChainDev<T>), &e);
+    MG_CUDA(c, e);
+    w.sw = dalloc(sizeof(uint32_t), &e);
+    MG_CUDA(c, e);
     LaunchArgs<T> none;  // set the adjoint kernels' attributes (outside any capture)
     std::memset(&none, 0, sizeof(none));
     MG_CUDA(c, launch_pass_yz<T>(n, sc->C, 3, none, c->stream));
     MG_CUDA(c, launch_pass_x<T>(n, 1, none, sc->B_max, c->stream));
     MG_CUDA(c, launch_pass_x<T>(n, 2, none, sc->B_max, c->stream));
   }
-  char* ckp = static_cast<char*>(ck->p);
+  if (!w.acc || w.B1 < B1) {
+    w.acc = dalloc(size_t(2) * B1 * sizeof(double), &e);
+    MG_CUDA(c, e);
+    w.Psave = dalloc(size_t(B1) * sizeof(double), &e);
+    MG_CUDA(c, e);
+    w.B1 = B1;
+  }
+  if (w.K_cap < K + 1) {
+    w.ck.reset();
+    w.ck = dalloc(state_b * size_t(K + 1), &e);
+    MG_CUDA(c, e);
+    w.K_cap = K + 1;
+  }
+  char* ckp = static_cast<char*>(w.ck->p);
   auto ck_main = [&](int k) { return reinterpret_cast<V2*>(ckp + size_t(k) * state_b); };
   auto ck_nyq = [&](int k) { return reinterpret_cast<V2*>(ckp + size_t(k) * state_b + main_b); };
-  V2* scr_main = static_cast<V2*>(scr->p);
-  V2* scr_nyq = reinterpret_cast<V2*>(static_cast<char*>(scr->p) + main_b);
-  V2* adj_main = static_cast<V2*>(adj->p);
-  V2* adj_nyq = reinterpret_cast<V2*>(static_cast<char*>(adj->p) + main_b);
+  V2* scr_main = static_cast<V2*>(w.scr->p);
+  V2* scr_nyq = reinterpret_cast<V2*>(static_cast<char*>(w.scr->p) + main_b);
+  V2* adj_main = static_cast<V2*>(w.adj->p);
+  V2* adj_nyq = reinterpret_cast<V2*>(static_cast<char*>(w.adj->p) + main_b);
   cudaStream_t s = c->stream;
+  uint32_t* ctr = static_cast<uint32_t*>(c->d_sweep->p);
+  const uint32_t* sw0 = static_cast<const uint32_t*>(w.sw->p);
 
-  // save the chain and set P = exp(logP)
-  uint32_t sw0 = 0;
-  MG_CUDA(c, cudaMemcpyAsync(&sw0, c->d_sweep->p, sizeof(sw0), cudaMemcpyDeviceToHost, s));
-  MG_CUDA(c, cudaMemcpyAsync(Psave->p, ch.P->p, size_t(B1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  MG_CUDA(c, cudaMemcpyAsync(ck_main(0), ch.main->p, main_b, cudaMemcpyDeviceToDevice, s));
-  MG_CUDA(c, cudaMemcpyAsync(ck_nyq(0), ch.nyq->p, nyq_b, cudaMemcpyDeviceToDevice, s));
+  // Host-to-device uploads first, while the stream holds no kernels (a copy
+  // from pageable memory waits for the stream): the loss weights, P =
+  // exp(logP) after saving the chain's P, and the four adjoint descriptors:
+  //   [0] the chain, [1] pass YZ recomputing t, [2] pass X of the last sweep,
+  //   [3] pass X of earlier sweeps, [4] the adjoint pass YZ.
+  MG_CUDA(c, cudaMemcpyAsync(w.wl64->p, wl_host, Mh * sizeof(double), cudaMemcpyHostToDevice, s));
+  adjoint_weights_kernel<T><<<1024, 256, 0, s>>>(static_cast<const double*>(w.wl64->p), n, static_cast<T*>(w.wl->p));
+  MG_CUDA(c, cudaGetLastError());
+  MG_CUDA(c, cudaMemcpyAsync(w.Psave->p, ch.P->p, size_t(B1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
   std::vector<double> Pn(B1);
   for (int b = 0; b < B1; ++b) Pn[b] = std::exp(logP[b]);
   MG_CUDA(c, cudaMemcpyAsync(ch.P->p, Pn.data(), size_t(B1) * sizeof(double), cudaMemcpyHostToDevice, s));
-  st = launch_shell_draw<T>(c, 0, false);
+  ChainDev<T> dsc[5] = {cd0, cd0, cd0, cd0, cd0};  // [0] unused (the chain's own is in d_desc)
+  dsc[1].main = scr_main;
+  dsc[1].nyq = scr_nyq;
+  for (int k = 2; k <= 3; ++k) {
+    dsc[k].main = adj_main;
+    dsc[k].nyq = adj_nyq;
+    dsc[k].main2 = scr_main;
+    dsc[k].nyq2 = scr_nyq;
+    dsc[k].wloss = static_cast<const T*>(w.wl->p);
+  }
+  dsc[2].main_in = ck_main(K);  // the last sweep starts from the final state
+  dsc[2].nyq_in = ck_nyq(K);
+  dsc[3].main_in = adj_main;  // earlier sweeps transform the adjoint state in place
+  dsc[3].nyq_in = adj_nyq;
+  dsc[4].main = adj_main;
+  dsc[4].nyq = adj_nyq;
+  dsc[4].dd = static_cast<T*>(w.dd->p);
+  MG_CUDA(c, cudaMemcpyAsync(w.desc->p, dsc, sizeof(dsc), cudaMemcpyHostToDevice, s));
+  const ChainDev<T>* dd_ = static_cast<const ChainDev<T>*>(w.desc->p);
+  LaunchArgs<T> as = base, ax_top = base, ax_mid = base, ay = base;
+  as.chains = dd_ + 1;
+  ax_top.chains = dd_ + 2;
+  ax_mid.chains = dd_ + 3;
+  ay.chains = dd_ + 4;
+
+  // save the chain (state, sweep counter) and draw its coefficients from P
+  MG_CUDA(c, cudaMemcpyAsync(w.sw->p, ctr, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  MG_CUDA(c, cudaMemcpyAsync(ck_main(0), ch.main->p, main_b, cudaMemcpyDeviceToDevice, s));
+  MG_CUDA(c, cudaMemcpyAsync(ck_nyq(0), ch.nyq->p, nyq_b, cudaMemcpyDeviceToDevice, s));
+  mg_status st = launch_shell_draw<T>(c, 0, false);
   if (st != MG_OK) return st;
-  // On the kz = 0 and n/2 planes both k and -k are stored; the loss counts
-  // each with its own weight, but the transforms act on the Hermitian part of a
-  // plane only, so the adjoint seed must use the pair's mean weight (the loss
-  // is the same since |s_hat(k)| = |s_hat(-k)|).
-  std::vector<T> wlt(Mh);
-  for (int kx = 0; kx < n; ++kx)
-    for (int ky = 0; ky < n; ++ky)
-      for (int kz = 0; kz <= H; ++kz) {
-        const size_t j = (size_t(kx) * n + ky) * (H + 1) + kz;
-        double wv = wl_host[j];
-        if (kz == 0 || kz == H) {
-          const size_t jp = (size_t((n - kx) % n) * n + (n - ky) % n) * (H + 1) + kz;
-          wv = 0.5 * (wl_host[j] + wl_host[jp]);
-        }
-        wlt[j] = T(wv);
-      }
-  MG_CUDA(c, cudaMemcpyAsync(wl->p, wlt.data(), Mh * sizeof(T), cudaMemcpyHostToDevice, s));
-  MG_CUDA(c, cudaMemsetAsync(dd->p, 0, g.M * sizeof(T), s));
-  MG_CUDA(c, cudaMemsetAsync(acc->p, 0, size_t(2) * B1 * sizeof(double), s));
+  MG_CUDA(c, cudaMemsetAsync(w.dd->p, 0, g.M * sizeof(T), s));
+  MG_CUDA(c, cudaMemsetAsync(w.acc->p, 0, size_t(2) * B1 * sizeof(double), s));
 
   // forward: K sweeps of this chain with P fixed, checkpointing every state
   for (int k = 1; k <= K; ++k) {
-    if ((st = set_sweep_ctr<T>(c, sw0 + uint32_t(k - 1))) != MG_OK) return st;
+    sweep_ctr_kernel<<<1, 32, 0, s>>>(ctr, sw0, uint32_t(k - 1));
     MG_CUDA(c, launch_pass_yz<T>(n, sc->C, 0, base, s));
     MG_CUDA(c, launch_pass_x<T>(n, 0, base, sc->B_max, s));
     MG_CUDA(c, cudaMemcpyAsync(ck_main(k), ch.main->p, main_b, cudaMemcpyDeviceToDevice, s));
@@ -820,31 +861,9 @@ mg_status adjoint_impl(mg_ctx* c, int chain, int K, const double* logP, const do
   }
 
   // adjoint sweeps K .. 1
-  ChainDev<T> cs = cd0, cx = cd0, cy = cd0;
-  cs.main = scr_main;
-  cs.nyq = scr_nyq;
-  cx.main = adj_main;
-  cx.nyq = adj_nyq;
-  cx.main2 = scr_main;
-  cx.nyq2 = scr_nyq;
-  cx.wloss = static_cast<const T*>(wl->p);
-  cy.main = adj_main;
-  cy.nyq = adj_nyq;
-  cy.gamma = static_cast<const T*>(g.gamma->p);
-  cy.dd = static_cast<T*>(dd->p);
-  std::shared_ptr<DevBuf> bs, bx_top, bx_mid, by;
-  LaunchArgs<T> as = base, ax_top = base, ax_mid = base, ay = base;
-  if ((st = upload_desc<T>(c, cs, &bs, &as)) != MG_OK) return st;
-  if ((st = upload_desc<T>(c, cy, &by, &ay)) != MG_OK) return st;
-  cx.main_in = ck_main(K);  // the last sweep starts from the final state
-  cx.nyq_in = ck_nyq(K);
-  if ((st = upload_desc<T>(c, cx, &bx_top, &ax_top)) != MG_OK) return st;
-  cx.main_in = adj_main;  // earlier sweeps transform the adjoint state in place
-  cx.nyq_in = adj_nyq;
-  if ((st = upload_desc<T>(c, cx, &bx_mid, &ax_mid)) != MG_OK) return st;
-  double* grad = static_cast<double*>(acc->p);
+  double* grad = static_cast<double*>(w.acc->p);
   for (int k = K; k >= 1; --k) {
-    if ((st = set_sweep_ctr<T>(c, sw0 + uint32_t(k - 1))) != MG_OK) return st;
+    sweep_ctr_kernel<<<1, 32, 0, s>>>(ctr, sw0, uint32_t(k - 1));
     // recompute the forward messenger field of sweep k: y/z transform of t_k
     MG_CUDA(c, cudaMemcpyAsync(scr_main, ck_main(k - 1), main_b, cudaMemcpyDeviceToDevice, s));
     MG_CUDA(c, cudaMemcpyAsync(scr_nyq, ck_nyq(k - 1), nyq_b, cudaMemcpyDeviceToDevice, s));
@@ -854,18 +873,21 @@ mg_status adjoint_impl(mg_ctx* c, int chain, int K, const double* logP, const do
     MG_CUDA(c, cudaGetLastError());
     MG_CUDA(c, launch_pass_yz<T>(n, sc->C, 3, ay, s));
   }
-  widen_kernel<T><<<1024, 256, 0, s>>>(static_cast<const T*>(dd->p), g.M, static_cast<double*>(ddw->p));
+  widen_kernel<T><<<1024, 256, 0, s>>>(static_cast<const T*>(w.dd->p), static_cast<const T*>(g.gamma->p), g.M,
+                                        static_cast<double*>(w.ddw->p));
+  MG_CUDA(c, cudaGetLastError());
+  // restore the chain, then read the results back (the pageable copies wait)
+  MG_CUDA(c, cudaMemcpyAsync(ch.main->p, ck_main(0), main_b, cudaMemcpyDeviceToDevice, s));
+  MG_CUDA(c, cudaMemcpyAsync(ch.nyq->p, ck_nyq(0), nyq_b, cudaMemcpyDeviceToDevice, s));
+  MG_CUDA(c, cudaMemcpyAsync(ch.P->p, w.Psave->p, size_t(B1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  st = launch_shell_draw<T>(c, 0, false);
+  if (st != MG_OK) return st;
+  sweep_ctr_kernel<<<1, 32, 0, s>>>(ctr, sw0, 0u);
   MG_CUDA(c, cudaGetLastError());
   std::vector<double> hb(size_t(2) * B1);
   MG_CUDA(c, cudaMemcpyAsync(hb.data(), grad, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-  MG_CUDA(c, cudaMemcpyAsync(dd_out, ddw->p, g.M * sizeof(double), cudaMemcpyDeviceToHost, s));
-  // restore the chain
-  MG_CUDA(c, cudaMemcpyAsync(ch.main->p, ck_main(0), main_b, cudaMemcpyDeviceToDevice, s));
-  MG_CUDA(c, cudaMemcpyAsync(ch.nyq->p, ck_nyq(0), nyq_b, cudaMemcpyDeviceToDevice, s));
-  MG_CUDA(c, cudaMemcpyAsync(ch.P->p, Psave->p, size_t(B1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  st = launch_shell_draw<T>(c, 0, false);
-  if (st != MG_OK) return st;
-  if ((st = set_sweep_ctr<T>(c, sw0)) != MG_OK) return st;
+  MG_CUDA(c, cudaMemcpyAsync(dd_out, w.ddw->p, g.M * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MG_CUDA(c, cudaStreamSynchronize(s));
   double L = 0.0;
   for (int b = 0; b < B1; ++b) {
     dlogP[b] = hb[b];
@@ -893,17 +915,24 @@ mg_status record_stats(mg_ctx* c) {
   for (size_t ci = 0; ci < c->chains.size(); ++ci) {
     const Group& g = c->groups[c->chains[ci].group];
     T* s = static_cast<T*>(c->d_scratch_s->p);
+    Chain& ch = c->chains[ci];
     SizeClass* sc;
-    std::shared_ptr<DevBuf> desc;
-    LaunchArgs<T> a;
-    mg_status st = single_chain_args<T>(c, int(ci), s, nullptr, &sc, &desc, &a);
-    if (st != MG_OK) return st;
+    size_t i;
+    if (!find_chain(c, int(ci), &sc, &i)) return fail(c, MG_EINVAL, "chain index out of range");
+    if (!ch.rec_desc) {  // the chain with the shared scratch field as output, made once
+      ChainDev<T> h = reinterpret_cast<const ChainDev<T>*>(sc->h_desc.data())[i];
+      h.s_out = s;
+      cudaError_t e;
+      ch.rec_desc = dalloc(sizeof(h), &e);
+      MG_CUDA(c, e);
+      MG_CUDA(c, cudaMemcpyAsync(ch.rec_desc->p, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    }
+    const LaunchArgs<T> a = one_chain_args<T>(*sc, i, static_cast<const ChainDev<T>*>(ch.rec_desc->p));
     MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, 1, a, c->stream));
     welford_kernel<T><<<1024, 256, 0, c->stream>>>(s, static_cast<double*>(c->chains[ci].mean->p),
                                                    static_cast<double*>(c->chains[ci].m2->p), g.M, inv);
     MG_CUDA(c, cudaGetLastError());
     // append P to the chain's trace (the buffer doubles when full)
-    Chain& ch = c->chains[ci];
     const size_t row = size_t(g.B + 1) * sizeof(double);
     if (c->records > ch.trace_cap) {
       const long long cap = std::max<long long>(64, 2 * ch.trace_cap);
@@ -919,7 +948,6 @@ mg_status record_stats(mg_ctx* c) {
     }
     MG_CUDA(c, cudaMemcpyAsync(static_cast<char*>(ch.trace->p) + size_t(c->records - 1) * row, ch.P->p, row,
                                cudaMemcpyDeviceToDevice, c->stream));
-    MG_CUDA(c, cudaStreamSynchronize(c->stream));
   }
   return MG_OK;
 }
@@ -1676,6 +1704,7 @@ void mg_destroy(mg_ctx* c) {
   c->groups.clear();
   c->d_draw.reset();
   c->d_pk_all.reset();
+  c->adj_work.clear();
   c->d_sweep.reset();
   c->d_status.reset();
   c->d_scratch_s.reset();

@@ -123,11 +123,39 @@ __global__ void adjoint_reduce_kernel(const double* __restrict__ partial, int n_
   }
 }
 
-// Widen the device-precision dL/dd to FP64 for the caller.
+// The sweep counter set on the device: *ctr = *base + add (no host round trip).
+__global__ void sweep_ctr_kernel(uint32_t* __restrict__ ctr, const uint32_t* __restrict__ base, uint32_t add) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *ctr = *base + add;
+}
+
+// The adjoint's loss weights in device precision.  On the kz = 0 and n/2
+// planes both k and -k are stored; the loss counts each with its own weight,
+// but the transforms act on the Hermitian part of a plane only, so the
+// adjoint seed uses the pair's mean weight (the loss is the same since
+// |s_hat(k)| = |s_hat(-k)|).
 template <typename T>
-__global__ void widen_kernel(const T* __restrict__ x, size_t M, double* __restrict__ y) {
+__global__ void adjoint_weights_kernel(const double* __restrict__ w, int n, T* __restrict__ out) {
+  const int H = n / 2;
+  const size_t total = size_t(n) * n * (H + 1);
+  for (size_t j = blockIdx.x * size_t(blockDim.x) + threadIdx.x; j < total; j += size_t(gridDim.x) * blockDim.x) {
+    const int kz = int(j % (H + 1));
+    const size_t r = j / (H + 1);
+    const int ky = int(r % n), kx = int(r / n);
+    double v = w[j];
+    if (kz == 0 || kz == H) {
+      const size_t jp = (size_t((n - kx) % n) * n + (n - ky) % n) * (H + 1) + kz;
+      v = 0.5 * (w[j] + w[jp]);
+    }
+    out[j] = T(v);
+  }
+}
+
+// dL/dd = gamma * (lam_t summed over the adjoint sweeps), widened to FP64
+// for the caller (gamma = dc/dd = tau R / (tau R^2 + N~), 0 unobserved).
+template <typename T>
+__global__ void widen_kernel(const T* __restrict__ x, const T* __restrict__ g, size_t M, double* __restrict__ y) {
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < M; i += size_t(gridDim.x) * blockDim.x)
-    y[i] = double(x[i]);
+    y[i] = double(g[i]) * double(x[i]);
 }
 
 // Shell draw and the next sweep's per-shell coefficients.  One CTA per

@@ -53,8 +53,8 @@ enum : int { kStNumeric = 1, kStTimeout = 2, kStBadInput = 4, kStNoObserved = 8 
 //   main[x][ky][kz]  kz in [0, n/2)  complex: the spectrum with x still in
 //                    real space (the x-transform is undone at the end of pass X)
 //   nyq[x][ky]                      complex: the kz = n/2 plane, same form
-// Group data (shared by all chains of one data set):
-//   bc[x][y][z]     (b, c) of the messenger draw t = c + b s + sqrt(tau b) g
+// Group data (shared by all chains of one data set), for the messenger draw
+// t = c + b s + sqrt(tau b) g:
 //   row_info[x][y]  (offset, lo | hi << 16): the z-range [lo, hi) of the row
 //                   that holds observed voxels (lo, hi multiples of 4), and
 //                   where it starts in bc_rows; unobserved voxels have b = 1,
@@ -65,7 +65,6 @@ template <typename T>
 struct ChainDev {
   typename VT<T>::c2* main;
   typename VT<T>::c2* nyq;
-  const typename VT<T>::c2* bc;
   const uint2* row_info;
   const typename VT<T>::c2* bc_rows;
   const typename VT<T>::c2* coef;  // [B+2]: (a / M, sd / sqrt(M)) per shell; [B+1] = DC
@@ -80,8 +79,7 @@ struct ChainDev {
   const typename VT<T>::c2* main2;    // pass X: the recomputed y/z transform of t
   const typename VT<T>::c2* nyq2;
   const T* wloss;                     // [n][n][n/2+1] loss weight per stored mode
-  const T* gamma;                     // [M] dc/dd = tau R / (tau R^2 + N~), 0 unobserved
-  T* dd;                              // [M] dL/dd accumulator
+  T* dd;                              // [M] sum of lam_t over the adjoint sweeps (observed rows)
   T tau;
   int B;
 };

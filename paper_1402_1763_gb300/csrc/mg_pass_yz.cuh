@@ -28,7 +28,7 @@ enum PassYZMode : int {
   kModeMaterialize = 1,  // inverse only, write s to ChainDev::s_out
   kModeLoad = 2,         // read s from ChainDev::s_in, forward only
   kModeAdjoint = 3,      // adjoint of the messenger step: inverse -> lam_t;
-                         // dd += gamma lam_t; b lam_t -> forward
+                         // dd += lam_t (observed rows only); b lam_t -> forward
 };
 
 template <typename T, int N, int C>
@@ -69,6 +69,28 @@ __device__ __forceinline__ cx<double> ld_dsmem(uint32_t addr, double) {
   cx<double> v;
   asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.re), "=d"(v.im) : "r"(addr) : "memory");
   return v;
+}
+
+// p[0..3] += (a.re, a.im, b.re, b.im) with vector accesses (p 16-byte
+// aligned for float, 32-byte for double).
+__device__ __forceinline__ void add4(float* p, cx<float> a, cx<float> b) {
+  float4* q = reinterpret_cast<float4*>(p);
+  float4 v = *q;
+  v.x += a.re;
+  v.y += a.im;
+  v.z += b.re;
+  v.w += b.im;
+  *q = v;
+}
+__device__ __forceinline__ void add4(double* p, cx<double> a, cx<double> b) {
+  double2* q = reinterpret_cast<double2*>(p);
+  double2 u = q[0], v = q[1];
+  u.x += a.re;
+  u.y += a.im;
+  v.x += b.re;
+  v.y += b.im;
+  q[0] = u;
+  q[1] = v;
 }
 
 template <int C>
@@ -367,9 +389,10 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
     // Messenger constants: only the row's observed z-range is stored; a
     // group of four voxels outside it has b = 1, c = 0 and needs no load.
     // Each group's constants are loaded ahead of their use (L2 latency).
+    constexpr bool kBC = MODE == kModeSweep || MODE == kModeAdjoint;  // uses (b, c)
     uint32_t lo = 0, hi = 0;
     const typename VT<T>::c2* brow = nullptr;
-    if constexpr (MODE == kModeSweep) {
+    if constexpr (kBC) {
       const uint2 ri = __ldg(cd.row_info + size_t(x) * N + y);
       lo = ri.y & 0xffffu;
       hi = ri.y >> 16;
@@ -386,7 +409,7 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
     // (FP32 only: in FP64 the second group in flight costs spills)
     constexpr int kAhead = sizeof(T) == 4 ? 2 : 1;
     cx<T> bc_next[4], bc_next2[4];
-    if constexpr (MODE == kModeSweep) {
+    if constexpr (kBC) {
       load_group(2 * pp, bc_next);
       if (kAhead == 2 && Q2 > 1) load_group(2 * (pp + P2), bc_next2);
     }
@@ -395,7 +418,7 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
       const int z0 = 2 * (pp + P2 * q);  // voxels z0 .. z0+3
       const size_t i0 = vox_row + z0;
       cx<T> bcv[4];
-      if constexpr (MODE == kModeSweep) {
+      if constexpr (kBC) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) bcv[k] = bc_next[k];
         if constexpr (kAhead == 2) {
@@ -423,13 +446,10 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
       } else if constexpr (MODE == kModeAdjoint) {
         // t = c + b s + sd g with c = gamma d: d receives gamma lam_t, s
         // receives b lam_t (the transposes of the per-voxel affine map).
-        ld_tw_row<T, 4>(cd.bc + i0, bcv);
-        T* dd = cd.dd + i0;
-        const T* gm = cd.gamma + i0;
-        dd[0] += gm[0] * Z0[q].re;
-        dd[1] += gm[1] * Z0[q].im;
-        dd[2] += gm[2] * Z1[q].re;
-        dd[3] += gm[3] * Z1[q].im;
+        // gamma is the same in every sweep and vanishes outside the row's
+        // observed range, so dd sums lam_t there only, over the K adjoint
+        // sweeps, and is multiplied by gamma once at the end.
+        if (uint32_t(z0) >= lo && uint32_t(z0) < hi) add4(cd.dd + i0, Z0[q], Z1[q]);
         Z0[q] = {bcv[0].re * Z0[q].re, bcv[1].re * Z0[q].im};
         Z1[q] = {bcv[2].re * Z1[q].re, bcv[3].re * Z1[q].im};
       } else {
