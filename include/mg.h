@@ -279,6 +279,22 @@ mg_status mg_tune(mg_ctx* ctx, int32_t reps);
  * at least 8 entries; any pointer may be NULL. */
 mg_status mg_schedule(mg_ctx* ctx, int32_t* n_sizes, int32_t* n, int32_t* yz_cluster, int32_t* persistent);
 
+/* The unit normals the sweep kernels make from Philox words (Box & Muller
+ * 1958 with U(w) = (2w + 1) 2^-33): for i in [0, n_pairs), the words
+ * wa = words_device[2i], wb = words_device[2i+1] give
+ *   out_device[3i]   = sqrt(-2 ln U(wa)) cos(2 pi U(wb)),
+ *   out_device[3i+1] = sqrt(-2 ln U(wa)) sin(2 pi U(wb)),
+ *   out_device[3i+2] = -2 ln U(wa)  (the pair's squared radius: the shell
+ *                                     sums' chi-square draw with 2 dof).
+ * precision 64: out_device holds doubles, made as the FP64 path makes them
+ * (table-driven logarithm, sine and cosine); precision 32: floats, as the
+ * FP32 path makes them (the special-function unit).  words_device: device
+ * memory of 2*n_pairs uint32; out_device: device memory of 3*n_pairs values.
+ * stream: cudaStream_t or NULL.  MG_EINVAL for another precision, a negative
+ * count or a NULL pointer with n_pairs > 0.  Synchronises. */
+mg_status mg_normals(int32_t precision, const uint32_t* words_device, int64_t n_pairs, void* out_device,
+                     void* stream);
+
 /* Raw Philox4x32-10 words on the device (Salmon et al. 2011; the per-core
  * generators of Sec. 3.4): for i in [0, n_calls), call i uses counter
  * (ctr0 + i, ctr1, ctr2, ctr3) and key (seed & 0xffffffff, seed >> 32) and

@@ -86,6 +86,7 @@ def library():
         "mg_destroy": (None, [_P]),
         "mg_philox": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int64,
                                 _P, _P]),
+        "mg_normals": (C.c_int, [C.c_int32, _P, C.c_int64, _P, _P]),
         "mg_shell_sums_noalloc": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P]),
         "mg_read_pk_trace": (C.c_int, [_P, C.c_int32, _D, C.c_int64, C.POINTER(C.c_int64)]),
         "mg_pk_acf": (C.c_int, [_P, C.c_int32, C.c_int32, _D, C.POINTER(C.c_int32)]),
@@ -292,6 +293,12 @@ def mg_last_error(ctx) -> str:
 
 def mg_destroy(ctx):
     library().mg_destroy(ctx)
+
+
+def mg_normals(precision: int, words_ptr: int, n_pairs: int, out_ptr: int, stream: int = 0):
+    """(z0, z1, -2 ln U(wa)) per word pair, as the kernels make them; device pointers."""
+    _check(library().mg_normals(int(precision), C.c_void_p(words_ptr), int(n_pairs), C.c_void_p(out_ptr),
+                                C.c_void_p(stream or None)))
 
 
 def mg_philox(seed: int, ctr0: int, ctr1: int, ctr2: int, ctr3: int, n_calls: int, out_ptr: int,

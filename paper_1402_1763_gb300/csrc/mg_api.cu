@@ -1712,6 +1712,22 @@ void mg_destroy(mg_ctx* c) {
   delete c;
 }
 
+mg_status mg_normals(int32_t precision, const uint32_t* words_device, int64_t n_pairs, void* out_device,
+                     void* stream) {
+  if ((precision != 64 && precision != 32) || n_pairs < 0) return MG_EINVAL;
+  if (n_pairs == 0) return MG_OK;
+  if (!words_device || !out_device) return MG_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int blocks = int(std::min<int64_t>((n_pairs + 255) / 256, 4096));
+  if (precision == 64)
+    normals_kernel<double><<<blocks, 256, 0, st>>>(words_device, (long long)n_pairs, static_cast<double*>(out_device));
+  else
+    normals_kernel<float><<<blocks, 256, 0, st>>>(words_device, (long long)n_pairs, static_cast<float*>(out_device));
+  if (cudaGetLastError() != cudaSuccess) return MG_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MG_ECUDA;
+  return MG_OK;
+}
+
 mg_status mg_philox(uint64_t seed, uint32_t ctr0, uint32_t ctr1, uint32_t ctr2, uint32_t ctr3, int64_t n_calls,
                     uint32_t* out_device, void* stream) {
   if (n_calls < 0 || (n_calls > 0 && !out_device)) return MG_EINVAL;

@@ -123,6 +123,20 @@ __global__ void adjoint_reduce_kernel(const double* __restrict__ partial, int n_
   }
 }
 
+// The kernels' unit normals from given Philox words (mg_normals).
+template <typename T>
+__global__ void normals_kernel(const uint32_t* __restrict__ words, long long n_pairs, T* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pairs;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint32_t wa = words[2 * i], wb = words[2 * i + 1];
+    T z0, z1;
+    normal_pair<T>(wa, wb, z0, z1);
+    out[3 * i] = z0;
+    out[3 * i + 1] = z1;
+    out[3 * i + 2] = radius2<T>(wa);
+  }
+}
+
 // The sweep counter set on the device: *ctr = *base + add (no host round trip).
 __global__ void sweep_ctr_kernel(uint32_t* __restrict__ ctr, const uint32_t* __restrict__ base, uint32_t add) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *ctr = *base + add;

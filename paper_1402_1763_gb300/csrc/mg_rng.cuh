@@ -12,6 +12,8 @@
 #pragma once
 #include <cstdint>
 
+#include "mg_rng_tables.h"
+
 namespace mg {
 
 struct u32x4 {
@@ -37,24 +39,73 @@ __device__ __forceinline__ u32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
   return {c0, c1, c2, c3};
 }
 
-// Box-Muller in FP64: U exactly (2w + 1) 2^-33.
-__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& z0, double& z1) {
-  const double ua = (2.0 * double(wa) + 1.0) * 0x1p-33;
-  const double ub = (2.0 * double(wb) + 1.0) * 0x1p-33;
-  const double r = sqrt(-2.0 * log(ua));
-  double s, c;
-  sincospi(2.0 * ub, &s, &c);
-  z0 = r * c;
-  z1 = r * s;
+// FP64 Box-Muller with U exactly (2w + 1) 2^-33.  Both transcendental
+// functions are table-driven (tables in mg_rng_tables.h, made in 40-digit
+// decimal arithmetic), taking the 33-bit integer v = 2w + 1 as it comes:
+//
+// ln U = ln v - 33 ln 2 (Tang 1990): v = 2^k m with m in [1, 2); F = 1 + j/128
+// the grid point nearest m (j from the 8 bits of m after the leading one),
+// f = m - F (exact, |f| <= 1/256), r = f / F, ln m = ln F + ln(1 + r) with
+// ln(1 + r) = r - r^2/2 + ... + r^7/7 - r^8/8 (|r| <= 2^-8; the first omitted
+// term is below 2^-67 r).  When m rounds to 2 it is halved instead (k + 1,
+// F = 1), so U just below 1 is ln(1 + r) alone, without cancellation.  The
+// sum (k - 33) ln 2 + ln F + ln(1 + r) is formed with ln 2 and ln F each split
+// in two, the high parts on one 2^-44 grid so that their sum is exact.
+//
+// sin, cos of 2 pi U: U = j/256 + t/(2 pi) with j the top 8 bits of v and
+// t = 2 pi (v mod 2^25) 2^-33 in [0, 2 pi/256); sin t and cos t - 1 by their
+// Taylor series to t^9 and t^8 (t < 0.0246: the omitted terms are below
+// 1e-20), then the angle-addition formulas with the table's sin, cos of
+// 2 pi j/256.  Accuracy is a few ulp, far inside the FP64 path's parity with
+// the oracle (relative L2 1e-12).
+__device__ __forceinline__ double ln_u33(uint32_t w) {
+  const unsigned long long v = 2ull * w + 1ull;  // 1 <= v < 2^33
+  int k = 63 - __clzll(static_cast<long long>(v));
+  const int q = k >= 8 ? int((v >> (k - 8)) & 255ull) : int((v << (8 - k)) & 255ull);
+  int j = (q + 1) >> 1;  // nearest grid point, 0 .. 128
+  double m = double(v) * __longlong_as_double(static_cast<long long>(1023 - k) << 52);  // exact
+  if (j == 128) {
+    j = 0;
+    k += 1;
+    m *= 0.5;
+  }
+  const double2 tab = __ldg(&kLnTab128[j]);  // {hi(ln F), 1/F}
+  const double lo = __ldg(&kLnLo128[j]);      // ln F - hi(ln F)
+  const double f = m - (1.0 + double(j) * 0x1p-7);
+  const double r = f * tab.y;
+  double p = fma(r, -1.0 / 8.0, 1.0 / 7.0);
+  p = fma(r, p, -1.0 / 6.0);
+  p = fma(r, p, 1.0 / 5.0);
+  p = fma(r, p, -1.0 / 4.0);
+  p = fma(r, p, 1.0 / 3.0);
+  p = fma(r, p, -0.5);
+  p = fma(r * r, p, r);  // ln(1 + r)
+  const double K = double(k - 33);
+  return fma(K, kLn2Hi, tab.x) + (fma(K, kLn2Lo, lo) + p);  // the first sum is exact
 }
 
-// Box-Muller in FP32: (2w + 1) rounded to nearest FP32, then scaled by 2^-33.
-__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& z0, float& z1) {
-  const float ua = __ull2float_rn(2ull * wa + 1ull) * 0x1p-33f;
-  const float ub = __ull2float_rn(2ull * wb + 1ull) * 0x1p-33f;
-  const float r = sqrtf(-2.0f * logf(ua));
-  float s, c;
-  sincospif(2.0f * ub, &s, &c);
+__device__ __forceinline__ void sincos_2pi_u33(uint32_t w, double& s, double& c) {
+  const unsigned long long v = 2ull * w + 1ull;
+  const int j = int(v >> 25);  // 0 .. 255
+  const double t = double(uint32_t(v & 0x1ffffffull)) * kTwoPi2m33;
+  const double t2 = t * t;
+  double ps = fma(t2, 1.0 / 362880.0, -1.0 / 5040.0);
+  ps = fma(t2, ps, 1.0 / 120.0);
+  ps = fma(t2, ps, -1.0 / 6.0);
+  const double st = fma(t * t2, ps, t);  // sin t
+  double pc = fma(t2, 1.0 / 40320.0, -1.0 / 720.0);
+  pc = fma(t2, pc, 1.0 / 24.0);
+  pc = fma(t2, pc, -0.5);
+  const double cm1 = t2 * pc;  // cos t - 1
+  const double2 tab = __ldg(&kSinCos256[j]);  // {sin, cos} of 2 pi j / 256
+  s = tab.x + fma(tab.x, cm1, tab.y * st);
+  c = tab.y + fma(tab.y, cm1, -(tab.x * st));
+}
+
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& z0, double& z1) {
+  const double r = sqrt(-2.0 * ln_u33(wa));
+  double s, c;
+  sincos_2pi_u33(wb, s, c);
   z0 = r * c;
   z1 = r * s;
 }
@@ -63,7 +114,9 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& z0, 
 // 2^-33); -2 ln U from the hardware base-2 logarithm; the angle 2 pi U is
 // shifted by pi into (-pi, pi] so the hardware sine and cosine stay in their
 // accurate range (|error| <= 2^-21.4 there).  The normals agree with the FP64
-// construction to ~1e-6 absolute.
+// construction to a few 1e-6 absolute, except as U_a -> 1, where U's FP32
+// rounding (relative 2^-23) moves -2 ln U by up to ~2^-22 and so the radius
+// by up to ~2^-22 / (2 r) (at most 5e-4, for radii below 1e-3).
 __device__ __forceinline__ float u01_fast(uint32_t w) { return fmaf(__uint2float_rn(w), 0x1p-32f, 0x1p-33f); }
 
 __device__ __forceinline__ float minus2log_fast(uint32_t w) { return -1.3862943611198906f * __log2f(u01_fast(w)); }
@@ -77,7 +130,7 @@ __device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float&
   z1 = -(r * s);
 }
 
-// Precision dispatch: FP64 uses the correctly rounded construction above, the
+// Precision dispatch: FP64 uses the table-driven construction above, the
 // FP32 path the special-function-unit one.
 template <typename T>
 __device__ __forceinline__ void normal_pair(uint32_t wa, uint32_t wb, T& z0, T& z1);
@@ -96,7 +149,7 @@ template <typename T>
 __device__ __forceinline__ T radius2(uint32_t w);
 template <>
 __device__ __forceinline__ double radius2<double>(uint32_t w) {
-  return -2.0 * log((2.0 * double(w) + 1.0) * 0x1p-33);
+  return -2.0 * ln_u33(w);
 }
 template <>
 __device__ __forceinline__ float radius2<float>(uint32_t w) {
