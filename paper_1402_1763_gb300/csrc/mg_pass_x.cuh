@@ -320,9 +320,9 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
 
   // Prefetch into L2 the pencils of the tile pf_units ahead in launch order
   // (CTAs start in launch order as earlier ones finish, so it starts soon),
-  // so its stage F1 loads hit L2 rather than HBM.  Main tiles only; lines
-  // that start past the last pencil are skipped.
-  if constexpr (!kAdj && !kMixScale) {
+  // so its first loads hit L2 rather than HBM.  Main tiles only; lines that
+  // start past the last pencil are skipped.
+  if constexpr (!kAdj) {
     const int nb = block + a.pf_units;
     if (a.pf_units > 0 && nb < S::kTiles * a.n_chains && nb % S::kTiles < S::kMainTiles) {
       const int f0 = (nb % S::kTiles) * LW;
