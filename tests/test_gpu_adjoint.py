@@ -8,6 +8,9 @@ through the C ABI and the torch.autograd binding.
   library on the same GPU, in every non-empty log P shell and along random
   directions in d; the chain state, P and sweep counter are unchanged after
   the call; the autograd binding returns the same gradients.
+* The work buffers kept between calls: a call after calls with a smaller K
+  (the checkpoints grow) and on another chain returns bit for bit what the
+  same call returns in a fresh context.
 """
 import numpy as np
 import pytest
@@ -96,3 +99,17 @@ def test_autograd_binding_returns_the_adjoint():
     assert float(L.detach()) == L_ref
     np.testing.assert_array_equal(lp.grad.numpy(), gl_ref)
     np.testing.assert_array_equal(d.grad.numpy(), gd_ref)
+
+
+def test_adjoint_buffers_reused_across_calls():
+    need_gpu()
+    m, prob, logP, w = copy_problem(16, 8, 7)
+    with gpu_sampler(m, 8, 7, 64, n_chains=2) as fresh:
+        L0, gl0, gd0 = fresh.adjoint(0, 5, logP, w)
+    with gpu_sampler(m, 8, 7, 64, n_chains=2) as g:
+        g.adjoint(0, 2, logP, w)
+        g.adjoint(1, 3, logP[::-1].copy(), w)
+        L, gl, gd = g.adjoint(0, 5, logP, w)
+    assert L == L0
+    np.testing.assert_array_equal(gl, gl0)
+    np.testing.assert_array_equal(gd, gd0)
