@@ -199,7 +199,8 @@ def tau_int(x) -> float:
 def run_other_workload(args):
     """Secondary workloads (not the headline line): the batching workload in
     one persistent launch per sweep, the adjoint of 8 sweeps at 128^3 FP32, the
-    plain FP64 sampler on the 128^3 grid with holes, mixing sweeps (Sec. 3.3)
+    plain FP64 sampler on the 128^3 grid with holes (alone, and against 16 FP32
+    chains on the same data), mixing sweeps (Sec. 3.3)
     on the 256^3 workload, and the P(k) autocorrelation of plain, mixing and
     alternating sweeps."""
     import torch
@@ -241,6 +242,29 @@ def run_other_workload(args):
                     value=dt * 1e3, unit="ms per call", higher_is_better=False, ms_per_step=dt * 1e3,
                     dtype="f32", config={"workload": w.name, "K": 8,
                                          "note": "host buffers in and out (weights, dL/dd); work buffers kept between calls"})
+    elif args.workload == "fp32-vs-fp64-128":
+        # the batched-FP32 / plain-FP64 ratio at 128^3 (the 128^3 data set
+        # with holes, 32 shells): 16 FP32 chains against 1 FP64 chain
+        w = mockgen.workload(2)
+        m = w.mocks[0]
+        res = {}
+        for prec, nc in ((32, 16), (64, 1)):
+            g = Sampler.single(m.n, m.L, m.N, m.R, m.d, m.n_bins, 2, precision=prec, n_chains=nc,
+                               stream=stream.cuda_stream)
+            g.sweep(args.warmup)
+            g.sync()
+            ev[0].record(stream)
+            g.sweep(args.steps)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1]) / args.steps
+            res[prec] = (nc * m.n ** 3 / (ms * 1e-3), ms)
+            g.close()
+        line.update(value=res[32][0], ms_per_step=res[32][1], dtype="f32",
+                    config={"workload": w.name.replace("fp64-1chain", "fp32-16chains-vs-fp64-1chain"),
+                            "chains": 16},
+                    fp64_single_chain={"value": res[64][0], "unit": UNIT, "ms_per_sweep": res[64][1]},
+                    batched_fp32_over_fp64=res[32][0] / res[64][0])
     elif args.workload == "fp64-128holes":
         w = mockgen.workload(2)
         m = w.mocks[0]
@@ -367,7 +391,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="256-fp32-16chains",
                     choices=["256-fp32-16chains", "batch-48chains", "adjoint-128", "fp64-128holes",
-                             "mixing-256", "mixing-acf", "precision-256"])
+                             "fp32-vs-fp64-128", "mixing-256", "mixing-acf", "precision-256"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = replicas.rank_world()
