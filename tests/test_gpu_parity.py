@@ -3,8 +3,9 @@
 Bars (relative L2 of each chain's field s and of its P, after each checkpoint):
 1e-12 for the FP64 path, 2e-5 for the FP32 path; Philox words bit-exact.
 Sizes cover a single tile, several tiles and non-power-of-two (ragged) lengths
-(12, 24, 48, 96 have a radix-3 factor), the 32^3 and 128^3 workloads in full
-form, and the 256^3 workload in the launch configuration the benchmark uses.
+(12, 24, 48, 96 have a radix-3 factor), the 32^3 workload over 200 sweeps and
+the 128^3 workload with holes over 100 (FP64), and the 256^3 workload in the
+launch configuration the benchmark uses.
 """
 import numpy as np
 import pytest
@@ -60,6 +61,17 @@ def test_workload_128cubed_holes(precision, cluster):
     res = compare_run(m, m.n_bins, 2, precision, [1, 3], yz_cluster=cluster)
     for cp, es, ep in res:
         assert es <= TOL[precision] and ep <= TOL[precision], (cp, es, ep)
+
+
+def test_workload_128cubed_holes_fp64_over_100_sweeps():
+    """The 128^3 FP64 workload with holes, draw for draw over 100 sweeps
+    (checkpoints 10, 30, 100): the FP64 bar holds as the chain moves."""
+    need_gpu()
+    w = mockgen.workload(2)
+    m = w.mocks[0]
+    res = compare_run(m, m.n_bins, 2, 64, [10, 30, 100])
+    for cp, es, ep in res:
+        assert es <= TOL[64] and ep <= TOL[64], (cp, es, ep)
 
 
 @pytest.mark.parametrize("precision,cluster", [(32, 2), (32, 4), (64, 4)])
