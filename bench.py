@@ -200,7 +200,8 @@ def run_other_workload(args):
     """Secondary workloads (not the headline line): the batching workload in
     one persistent launch per sweep, the adjoint of 8 sweeps at 128^3 FP32, the
     plain FP64 sampler on the 128^3 grid with holes (alone, and against 16 FP32
-    chains on the same data), mixing sweeps (Sec. 3.3)
+    chains on the same data), the 256^3 sweeps with every sweep recorded (mean
+    and variance maps, P(k) trace), mixing sweeps (Sec. 3.3)
     on the 256^3 workload, and the P(k) autocorrelation of plain, mixing and
     alternating sweeps."""
     import torch
@@ -265,6 +266,27 @@ def run_other_workload(args):
                             "chains": 16},
                     fp64_single_chain={"value": res[64][0], "unit": UNIT, "ms_per_sweep": res[64][1]},
                     batched_fp32_over_fp64=res[32][0] / res[64][0])
+    elif args.workload == "record-256":
+        # full-rate posterior summaries: the 256^3 workload (16 FP32 chains)
+        # with every sweep recorded (FP64 running mean and variance maps of s
+        # and the P(k) trace of every chain), against the same sweeps unrecorded
+        w = mockgen.workload(3)
+        m = w.mocks[0]
+        res = {}
+        for rec in (1, 0):
+            g = Sampler.single(m.n, m.L, m.N, m.R, m.d, m.n_bins, 3, precision=32, n_chains=16,
+                               record_every=rec, stream=stream.cuda_stream)
+            g.sweep(args.warmup)
+            g.sync()
+            ev[0].record(stream)
+            g.sweep(args.steps)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            res[rec] = ev[0].elapsed_time(ev[1]) / args.steps
+            g.close()
+        line.update(value=16 * m.n ** 3 / (res[1] * 1e-3), ms_per_step=res[1], dtype="f32",
+                    config={"workload": w.name + "-record-every-sweep", "chains": 16},
+                    ms_per_step_unrecorded=res[0])
     elif args.workload == "fp64-128holes":
         w = mockgen.workload(2)
         m = w.mocks[0]
@@ -391,7 +413,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="256-fp32-16chains",
                     choices=["256-fp32-16chains", "batch-48chains", "adjoint-128", "fp64-128holes",
-                             "fp32-vs-fp64-128", "mixing-256", "mixing-acf", "precision-256"])
+                             "fp32-vs-fp64-128", "record-256", "mixing-256", "mixing-acf", "precision-256"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = replicas.rank_world()
