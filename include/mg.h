@@ -74,10 +74,14 @@ typedef struct {
   double tau_scale;       /* in (0, 1]: tau = tau_scale * min N_i/R_i^2.     */
   const double* P0;       /* n_bins+1 starting powers shared by all chains, or
                              NULL for flat S_hat = 1 (P = V/M).               */
-  int32_t record_every;   /* >0: accumulate per-voxel mean/variance of s and a
-                             P(k) trace every record_every-th sweep of
-                             mg_sweep (see mg_read_pk_trace, mg_pk_acf,
-                             mg_pk_quantiles); 0 = off.                       */
+  int32_t record_every;   /* >0: the state after every record_every-th sweep
+                             of mg_sweep is a sample: its s goes into per-voxel
+                             FP64 sums of s and s^2 (mean/var of
+                             mg_read_stats; added inside the next sweep, or
+                             when read or replaced first) and its P(k) into
+                             the trace (mg_read_pk_trace, mg_pk_acf,
+                             mg_pk_quantiles); 0 = off.  mg_sweep_timed
+                             records nothing.                                 */
   int32_t fix_P;          /* nonzero: hold P fixed (signal sampler only).     */
   int64_t timeout_cycles; /* budget of device-side waits in clock cycles;
                              0 = library default.                            */
@@ -126,8 +130,10 @@ typedef struct {
   double* chi_b;          /* [n_bins+1] last sweep's chi-square draw X_b; with
                              mixing sweeps: 1 where the shell's proposal was
                              accepted, else 0                                 */
-  double* mean;           /* [M] per-voxel posterior mean of s (out)          */
-  double* var;            /* [M] per-voxel posterior variance of s (out)      */
+  double* mean;           /* [M] per-voxel posterior mean of s over the
+                             recorded samples, S1/n (out)                    */
+  double* var;            /* [M] their variance (S2 - S1 mean)/(n-1), 0 for
+                             n < 2 (out)                                     */
 } mg_stats;
 
 /* Fill *opt with the defaults listed in mg_options. */

@@ -47,7 +47,8 @@ struct Group {
 struct Chain {
   int group = 0;
   uint32_t chain_id = 0;
-  std::shared_ptr<DevBuf> main, nyq, coef, mscale, partial, P, sig, chi, mean, m2;
+  std::shared_ptr<DevBuf> main, nyq, coef, mscale, partial, P, sig, chi;
+  std::shared_ptr<DevBuf> s1, s2;  // [M] FP64 sums of the recorded samples of s and of s^2
   std::shared_ptr<DevBuf> rec_desc;  // the chain's descriptor with the scratch field as output
   std::shared_ptr<DevBuf> trace;  // [records][B+1] P after every record_every-th sweep
   long long trace_cap = 0;        // records the trace buffer holds
@@ -88,6 +89,8 @@ struct mg_ctx {
   std::shared_ptr<DevBuf> d_draw;  // DrawDev[chains]
   std::shared_ptr<DevBuf> d_sweep, d_status, d_scratch_s;
   std::shared_ptr<DevBuf> d_pk_all;  // staging of mg_read_pk_all
+  std::shared_ptr<DevBuf> d_rec_now;  // int: the next pass YZ adds its incoming state to the sums
+  bool stats_pending = false;         // the current state is a recorded sample not yet in the sums
   std::map<int, AdjWork> adj_work;   // mg_adjoint's buffers per grid size
   int B_max = 0;
   long long sweeps = 0;
@@ -257,6 +260,8 @@ mg_status upload_descriptors(mg_ctx* c) {
       d.mscale = static_cast<const T*>(ch.mscale->p);
       d.partial = static_cast<double*>(ch.partial->p);
       d.bin_of_m2 = static_cast<const uint8_t*>(g.bin_of_m2->p);
+      d.s1 = ch.s1 ? static_cast<double*>(ch.s1->p) : nullptr;
+      d.s2 = ch.s2 ? static_cast<double*>(ch.s2->p) : nullptr;
       d.s_out = nullptr;
       d.s_in = nullptr;
       d.tau = T(g.tau);
@@ -278,6 +283,7 @@ mg_status upload_descriptors(mg_ctx* c) {
       a.chains = static_cast<const ChainDev<T>*>(sc.d_desc->p) + c0;
       a.sweep_ctr = static_cast<const uint32_t*>(c->d_sweep->p);
       a.tw = static_cast<const V2*>(sc.tw->p);
+      a.rec_now = static_cast<const int*>(c->d_rec_now->p);
       a.n_chains = int(std::min<size_t>(kMaxLaunchChains, sc.chains.size() - c0));
       for (int k = 0; k < a.n_chains; ++k) {
         const Chain& ch = c->chains[sc.chains[c0 + k]];
@@ -361,13 +367,19 @@ mg_status for_each_class(mg_ctx* c, F fn) {
   return MG_OK;
 }
 
+// Recorded samples are added to the sums inside the next sweep's pass YZ
+// (its record mode), except under the persistent schedule, which adds them
+// with a separate pass right after the sweep.
+bool fused_record(const mg_ctx* c) { return c->record_every > 0 && !c->persist; }
+
 // which: bit 1 = pass YZ of every size class, bit 2 = pass X, bit 4 = shell draw.
 // A whole sweep (which = 7) runs each size class's passes as its own branch.
 template <typename T>
 mg_status enqueue_passes(mg_ctx* c, int which, bool mix) {
-  auto yz = [c](SizeClass& sc, cudaStream_t st) -> mg_status {
+  const int yz_mode = fused_record(c) ? int(kModeSweepRecord) : int(kModeSweep);
+  auto yz = [c, yz_mode](SizeClass& sc, cudaStream_t st) -> mg_status {
     for (auto& blob : sc.args)
-      MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, 0, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()), st));
+      MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, yz_mode, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()), st));
     return MG_OK;
   };
   auto xpass = [c](int mode) {
@@ -405,7 +417,8 @@ mg_status enqueue_passes(mg_ctx* c, int which, bool mix) {
   if (which & 1) {
     for (auto& sc : c->classes)
       for (auto& blob : sc.args)
-        MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, 0, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()), c->stream));
+        MG_CUDA(c, launch_pass_yz<T>(sc.n, sc.C, yz_mode, *reinterpret_cast<const LaunchArgs<T>*>(blob.data()),
+                                     c->stream));
   }
   if (mix) {
     // mixing sweep: x draw and its shell sums (modes left in k space), the
@@ -537,10 +550,18 @@ std::string tune_key(const mg_ctx* c) {
   return k;
 }
 
+mg_status flush_stats(mg_ctx* c);
+
 template <typename T>
 mg_status tune_impl(mg_ctx* c, int reps) {
   using V2 = typename VT<T>::c2;
   if (reps < 1) reps = 1;
+  {
+    // the trial sweeps must not add anything to the sums
+    const mg_status fs = flush_stats(c);
+    if (fs != MG_OK) return fs;
+    MG_CUDA(c, cudaMemsetAsync(c->d_rec_now->p, 0, sizeof(int), c->stream));
+  }
   const std::string key = tune_key(c);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -679,6 +700,7 @@ LaunchArgs<T> one_chain_args(const SizeClass& sc, size_t i, const ChainDev<T>* d
   a.chains = dev;
   a.sweep_ctr = src.sweep_ctr;
   a.tw = src.tw;
+  a.rec_now = src.rec_now;
   a.n_chains = 1;
   a.k0[0] = src.k0[i % kMaxLaunchChains];
   a.k1[0] = src.k1[i % kMaxLaunchChains];
@@ -908,10 +930,10 @@ mg_status check_status(mg_ctx* c) {
   return MG_OK;
 }
 
+// Add the current state of every chain to its sums: materialise s into the
+// shared scratch field, then add it (the fallback of the fused record mode).
 template <typename T>
-mg_status record_stats(mg_ctx* c) {
-  ++c->records;
-  const double inv = 1.0 / double(c->records);
+mg_status accumulate_now(mg_ctx* c) {
   for (size_t ci = 0; ci < c->chains.size(); ++ci) {
     const Group& g = c->groups[c->chains[ci].group];
     T* s = static_cast<T*>(c->d_scratch_s->p);
@@ -928,11 +950,18 @@ mg_status record_stats(mg_ctx* c) {
       MG_CUDA(c, cudaMemcpyAsync(ch.rec_desc->p, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
     }
     const LaunchArgs<T> a = one_chain_args<T>(*sc, i, static_cast<const ChainDev<T>*>(ch.rec_desc->p));
-    MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, 1, a, c->stream));
-    welford_kernel<T><<<1024, 256, 0, c->stream>>>(s, static_cast<double*>(c->chains[ci].mean->p),
-                                                   static_cast<double*>(c->chains[ci].m2->p), g.M, inv);
+    MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, kModeMaterialize, a, c->stream));
+    moments_kernel<T><<<1024, 256, 0, c->stream>>>(s, static_cast<double*>(ch.s1->p), static_cast<double*>(ch.s2->p),
+                                                   g.M);
     MG_CUDA(c, cudaGetLastError());
-    // append P to the chain's trace (the buffer doubles when full)
+  }
+  return MG_OK;
+}
+
+// Append every chain's P to its trace (the buffer doubles when full).
+mg_status append_trace(mg_ctx* c) {
+  for (auto& ch : c->chains) {
+    const Group& g = c->groups[ch.group];
     const size_t row = size_t(g.B + 1) * sizeof(double);
     if (c->records > ch.trace_cap) {
       const long long cap = std::max<long long>(64, 2 * ch.trace_cap);
@@ -949,6 +978,31 @@ mg_status record_stats(mg_ctx* c) {
     MG_CUDA(c, cudaMemcpyAsync(static_cast<char*>(ch.trace->p) + size_t(c->records - 1) * row, ch.P->p, row,
                                cudaMemcpyDeviceToDevice, c->stream));
   }
+  return MG_OK;
+}
+
+// After a sweep that ends a record interval: P goes to the trace now; the new
+// state goes into the sums inside the next sweep's pass YZ (or now, under the
+// persistent schedule).
+template <typename T>
+mg_status record_sweep(mg_ctx* c) {
+  ++c->records;
+  mg_status st = append_trace(c);
+  if (st != MG_OK) return st;
+  if (fused_record(c)) {
+    c->stats_pending = true;
+    return MG_OK;
+  }
+  return accumulate_now<T>(c);
+}
+
+// A recorded sample still waiting for the next sweep is added now: before
+// the sums are read, the state is replaced, or sweeps run that do not record.
+mg_status flush_stats(mg_ctx* c) {
+  if (!c->stats_pending) return MG_OK;
+  const mg_status st = c->precision == 32 ? accumulate_now<float>(c) : accumulate_now<double>(c);
+  if (st != MG_OK) return st;
+  c->stats_pending = false;
   return MG_OK;
 }
 
@@ -971,6 +1025,9 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
   MG_CUDA(c, e);
   c->d_status = dalloc(sizeof(int), &e);
   MG_CUDA(c, e);
+  c->d_rec_now = dalloc(sizeof(int), &e);
+  MG_CUDA(c, e);
+  MG_CUDA(c, cudaMemsetAsync(c->d_rec_now->p, 0, sizeof(int), c->stream));
   MG_CUDA(c, cudaMemsetAsync(c->d_sweep->p, 0, sizeof(uint32_t), c->stream));
   MG_CUDA(c, cudaMemsetAsync(c->d_status->p, 0, sizeof(int), c->stream));
   size_t max_M = 0;
@@ -1129,12 +1186,12 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
         MG_CUDA(c, cudaGetLastError());
       }
       if (c->record_every > 0) {
-        ch.mean = dalloc(gg.M * sizeof(double), &e);
+        ch.s1 = dalloc(gg.M * sizeof(double), &e);
         MG_CUDA(c, e);
-        ch.m2 = dalloc(gg.M * sizeof(double), &e);
+        ch.s2 = dalloc(gg.M * sizeof(double), &e);
         MG_CUDA(c, e);
-        MG_CUDA(c, cudaMemsetAsync(ch.mean->p, 0, gg.M * sizeof(double), c->stream));
-        MG_CUDA(c, cudaMemsetAsync(ch.m2->p, 0, gg.M * sizeof(double), c->stream));
+        MG_CUDA(c, cudaMemsetAsync(ch.s1->p, 0, gg.M * sizeof(double), c->stream));
+        MG_CUDA(c, cudaMemsetAsync(ch.s2->p, 0, gg.M * sizeof(double), c->stream));
       }
       c->classes[class_of_n[gg.n]].chains.push_back(int(c->chains.size()));
       c->chains.push_back(std::move(ch));
@@ -1304,6 +1361,10 @@ mg_status mg_sweep(mg_ctx* c, int64_t n) {
   for (int64_t i = 0; i < n; ++i) {
     mg_status s = MG_OK;
     const bool mix = mixing_sweep_next(c);
+    const bool fused = fused_record(c);
+    // the record mode of pass YZ adds its incoming state to the sums iff it
+    // is a recorded sample not yet added
+    if (fused) MG_CUDA(c, cudaMemsetAsync(c->d_rec_now->p, c->stats_pending ? 1 : 0, sizeof(int), c->stream));
     cudaGraphExec_t& graph = mix ? c->graph_mix : c->graph;
     if (!graph && !c->graph_failed) {
       cudaGraph_t g;
@@ -1332,9 +1393,10 @@ mg_status mg_sweep(mg_ctx* c, int64_t n) {
       s = enqueue_sweep(c, mix);
       if (s != MG_OK) return s;
     }
+    if (fused) c->stats_pending = false;
     ++c->sweeps;
     if (c->record_every > 0 && c->sweeps % c->record_every == 0) {
-      s = c->precision == 32 ? record_stats<float>(c) : record_stats<double>(c);
+      s = c->precision == 32 ? record_sweep<float>(c) : record_sweep<double>(c);
       if (s != MG_OK) return s;
     }
   }
@@ -1345,6 +1407,10 @@ mg_status mg_sweep_timed(mg_ctx* c, int64_t n, double* ms_out) {
   if (!c || !ms_out) return MG_EINVAL;
   if (c->sticky != MG_OK) return c->sticky;
   if (n < 0) return fail(c, MG_EINVAL, "n_sweeps must be >= 0");
+  // timed sweeps record nothing: a pending sample is added first
+  mg_status fs = flush_stats(c);
+  if (fs != MG_OK) return fs;
+  if (c->d_rec_now) MG_CUDA(c, cudaMemsetAsync(c->d_rec_now->p, 0, sizeof(int), c->stream));
   cudaEvent_t ev[4];
   for (auto& e : ev) MG_CUDA(c, cudaEventCreate(&e));
   for (int64_t i = 0; i < n; ++i) {
@@ -1435,18 +1501,26 @@ mg_status mg_read_stats(mg_ctx* c, int32_t chain, mg_stats* out) {
   const size_t nb = size_t(g.B + 1) * sizeof(double);
   if (out->sigma_b) MG_CUDA(c, cudaMemcpyAsync(out->sigma_b, ch.sig->p, nb, cudaMemcpyDeviceToHost, c->stream));
   if (out->chi_b) MG_CUDA(c, cudaMemcpyAsync(out->chi_b, ch.chi->p, nb, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<double> s1;
   if (out->mean || out->var) {
     if (c->record_every <= 0) return fail(c, MG_ESTATE, "mean/var need record_every > 0");
-    if (out->mean)
-      MG_CUDA(c, cudaMemcpyAsync(out->mean, ch.mean->p, g.M * 8, cudaMemcpyDeviceToHost, c->stream));
-    if (out->var) {
-      MG_CUDA(c, cudaMemcpyAsync(out->var, ch.m2->p, g.M * 8, cudaMemcpyDeviceToHost, c->stream));
-    }
+    const mg_status fs = flush_stats(c);
+    if (fs != MG_OK) return fs;
+    s1.resize(g.M);
+    MG_CUDA(c, cudaMemcpyAsync(s1.data(), ch.s1->p, g.M * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (out->var) MG_CUDA(c, cudaMemcpyAsync(out->var, ch.s2->p, g.M * 8, cudaMemcpyDeviceToHost, c->stream));
   }
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (out->var) {
-    const double inv = c->records > 1 ? 1.0 / double(c->records - 1) : 0.0;
-    for (size_t i = 0; i < g.M; ++i) out->var[i] *= inv;
+  if (!s1.empty()) {
+    // mean = S1 / n, var = (S2 - S1 mean) / (n - 1) over the n recorded samples
+    const double n_rec = double(c->records);
+    const double inv_n = c->records > 0 ? 1.0 / n_rec : 0.0;
+    const double inv_n1 = c->records > 1 ? 1.0 / (n_rec - 1.0) : 0.0;
+    for (size_t i = 0; i < g.M; ++i) {
+      const double mu = s1[i] * inv_n;
+      if (out->mean) out->mean[i] = mu;
+      if (out->var) out->var[i] = std::max(0.0, (out->var[i] - s1[i] * mu) * inv_n1);
+    }
   }
   return check_status(c);
 }
@@ -1457,6 +1531,10 @@ mg_status mg_set_s(mg_ctx* c, int32_t chain, const void* s_in, int32_t s_is_devi
   if (!valid_chain(c, chain)) return fail(c, MG_EINVAL, "chain index out of range");
   const Group& g = c->groups[c->chains[chain].group];
   const size_t es = c->precision == 32 ? 4 : 8;
+  {
+    const mg_status fs = flush_stats(c);  // a pending sample is the state about to be replaced
+    if (fs != MG_OK) return fs;
+  }
   const void* src = s_in;
   std::shared_ptr<DevBuf> tmp;
   if (!s_is_device) {

@@ -368,17 +368,14 @@ __global__ void gather_pk_kernel(const DrawDev* __restrict__ chains, int B1max, 
 // Advance the device sweep counter (end of a mixing sweep).
 __global__ void sweep_bump_kernel(uint32_t* sweep_ctr) { atomicAdd(sweep_ctr, 1u); }
 
-// Welford update of the per-voxel mean and sum of squared deviations of s.
+// One recorded sample s added to the per-voxel FP64 sums of s and s^2 (the
+// record mode of pass YZ does the same inside the sweep).
 template <typename T>
-__global__ void welford_kernel(const T* __restrict__ s, double* __restrict__ mean, double* __restrict__ m2,
-                               size_t M, double inv_count) {
+__global__ void moments_kernel(const T* __restrict__ s, double* __restrict__ s1, double* __restrict__ s2, size_t M) {
   for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < M; i += size_t(gridDim.x) * blockDim.x) {
     const double x = double(s[i]);
-    const double mu = mean[i];
-    const double dlt = x - mu;
-    const double mu2 = mu + dlt * inv_count;
-    mean[i] = mu2;
-    m2[i] += dlt * (x - mu2);
+    s1[i] += x;
+    s2[i] = fma(x, x, s2[i]);
   }
 }
 

@@ -46,6 +46,17 @@ __device__ __forceinline__ void stc(typename VT<T>::c2* p, cx<T> a) {
 __device__ __forceinline__ double msg_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float msg_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 
+// Modes of pass YZ (mg_pass_yz.cuh).
+enum PassYZMode : int {
+  kModeSweep = 0,        // inverse -> messenger draw -> forward (the hot path)
+  kModeMaterialize = 1,  // inverse only, write s to ChainDev::s_out
+  kModeLoad = 2,         // read s from ChainDev::s_in, forward only
+  kModeAdjoint = 3,      // adjoint of the messenger step: inverse -> lam_t;
+                         // dd += lam_t (observed rows only); b lam_t -> forward
+  kModeSweepRecord = 4,  // kModeSweep that also adds the incoming s to the
+                         // chain's sums (s1, s2) when *rec_now is set
+};
+
 // Device status bits (sticky on the context once read by the host).
 enum : int { kStNumeric = 1, kStTimeout = 2, kStBadInput = 4, kStNoObserved = 8 };
 
@@ -80,6 +91,8 @@ struct ChainDev {
   const typename VT<T>::c2* nyq2;
   const T* wloss;                     // [n][n][n/2+1] loss weight per stored mode
   T* dd;                              // [M] sum of lam_t over the adjoint sweeps (observed rows)
+  double* s1;                         // [M] sum of the recorded samples of s (record_every > 0)
+  double* s2;                         // [M] sum of their squares
   T tau;
   int B;
 };
@@ -95,6 +108,7 @@ struct LaunchArgs {
   const typename VT<T>::c2* tw;  // twiddle tables of this grid size (TwLayout)
   int n_chains;
   int pf_units;  // pass X: prefetch into L2 the input of tile + pf_units (0: none)
+  const int* rec_now;  // pass YZ record mode: nonzero if the incoming state is a sample to add
   uint32_t k0[kMaxLaunchChains];
   uint32_t k1[kMaxLaunchChains];
   uint32_t cid[kMaxLaunchChains];

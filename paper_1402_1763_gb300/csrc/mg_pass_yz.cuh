@@ -23,13 +23,6 @@ namespace mg {
 
 namespace cg = cooperative_groups;
 
-enum PassYZMode : int {
-  kModeSweep = 0,        // inverse -> messenger draw -> forward (the hot path)
-  kModeMaterialize = 1,  // inverse only, write s to ChainDev::s_out
-  kModeLoad = 2,         // read s from ChainDev::s_in, forward only
-  kModeAdjoint = 3,      // adjoint of the messenger step: inverse -> lam_t;
-                         // dd += lam_t (observed rows only); b lam_t -> forward
-};
 
 template <typename T, int N, int C>
 struct PassYZShape {
@@ -93,6 +86,29 @@ __device__ __forceinline__ void add4(double* p, cx<double> a, cx<double> b) {
   q[1] = v;
 }
 
+// s1[0..3] += x, s2[0..3] += x^2 in FP64 for the four voxels x = (a.re,
+// a.im, b.re, b.im) (s1, s2 32-byte aligned).  The same arithmetic as
+// moments_kernel, so fused and separate accumulation agree bit for bit.
+template <typename T>
+__device__ __forceinline__ void add_moments(double* s1, double* s2, cx<T> a, cx<T> b) {
+  double2* p1 = reinterpret_cast<double2*>(s1);
+  double2* p2 = reinterpret_cast<double2*>(s2);
+  const double x0 = double(a.re), x1 = double(a.im), x2 = double(b.re), x3 = double(b.im);
+  double2 u = p1[0], v = p1[1], w = p2[0], z = p2[1];
+  u.x += x0;
+  u.y += x1;
+  v.x += x2;
+  v.y += x3;
+  w.x = fma(x0, x0, w.x);
+  w.y = fma(x1, x1, w.y);
+  z.x = fma(x2, x2, z.x);
+  z.y = fma(x3, x3, z.y);
+  p1[0] = u;
+  p1[1] = v;
+  p2[0] = w;
+  p2[1] = z;
+}
+
 template <int C>
 __device__ __forceinline__ void cluster_barrier() {
   if constexpr (C == 1) {
@@ -154,6 +170,8 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
   V2* nyqp = cd.nyq + size_t(x) * N;
   const uint32_t sweep = *a.sweep_ctr;
   const T tau = cd.tau;
+  bool rec = false;
+  if constexpr (MODE == kModeSweepRecord) rec = *a.rec_now != 0;
 
   // Every CTA of the cluster must be running before another writes into its
   // shared memory.  The arrive needs no ordering; the wait comes after this
@@ -389,7 +407,7 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
     // Messenger constants: only the row's observed z-range is stored; a
     // group of four voxels outside it has b = 1, c = 0 and needs no load.
     // Each group's constants are loaded ahead of their use (L2 latency).
-    constexpr bool kBC = MODE == kModeSweep || MODE == kModeAdjoint;  // uses (b, c)
+    constexpr bool kBC = MODE == kModeSweep || MODE == kModeSweepRecord || MODE == kModeAdjoint;  // uses (b, c)
     uint32_t lo = 0, hi = 0;
     const typename VT<T>::c2* brow = nullptr;
     if constexpr (kBC) {
@@ -453,6 +471,11 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
         Z0[q] = {bcv[0].re * Z0[q].re, bcv[1].re * Z0[q].im};
         Z1[q] = {bcv[2].re * Z1[q].re, bcv[3].re * Z1[q].im};
       } else {
+        if constexpr (MODE == kModeSweepRecord) {
+          // the incoming state is a recorded sample: its s (exactly what the
+          // materialise pass writes) goes into the FP64 sums of s and s^2
+          if (rec) add_moments(cd.s1 + i0, cd.s2 + i0, Z0[q], Z1[q]);
+        }
         const u32x4 w = philox4x32_10(uint32_t(i0 >> 2), sweep, cid, kStreamMessenger, k0, k1);
         T g0, g1, g2, g3;
         normal_pair<T>(w.x, w.y, g0, g1);

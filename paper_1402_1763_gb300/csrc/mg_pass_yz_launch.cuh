@@ -52,6 +52,8 @@ cudaError_t run_mode(int mode, const LaunchArgs<T>& args, cudaStream_t st) {
       return run<T, N, C, kModeLoad>(args, st);
     case kModeAdjoint:
       return run<T, N, C, kModeAdjoint>(args, st);
+    case kModeSweepRecord:
+      return run<T, N, C, kModeSweepRecord>(args, st);
     default:
       return cudaErrorInvalidValue;
   }
