@@ -1511,6 +1511,18 @@ mg_status mg_read_stats(mg_ctx* c, int32_t chain, mg_stats* out) {
     if (out->var) MG_CUDA(c, cudaMemcpyAsync(out->var, ch.s2->p, g.M * 8, cudaMemcpyDeviceToHost, c->stream));
   }
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (!s1.empty() && c->precision == 32) {
+    // FP32 chains keep each sum as a (hi, lo) pair of floats
+    auto widen = [](double* v, size_t n) {
+      for (size_t i = 0; i < n; ++i) {
+        float hl[2];
+        std::memcpy(hl, v + i, sizeof(hl));
+        v[i] = double(hl[0]) + double(hl[1]);
+      }
+    };
+    widen(s1.data(), g.M);
+    if (out->var) widen(out->var, g.M);
+  }
   if (!s1.empty()) {
     // mean = S1 / n, var = (S2 - S1 mean) / (n - 1) over the n recorded samples
     const double n_rec = double(c->records);

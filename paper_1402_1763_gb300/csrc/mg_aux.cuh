@@ -368,15 +368,29 @@ __global__ void gather_pk_kernel(const DrawDev* __restrict__ chains, int B1max, 
 // Advance the device sweep counter (end of a mixing sweep).
 __global__ void sweep_bump_kernel(uint32_t* sweep_ctr) { atomicAdd(sweep_ctr, 1u); }
 
-// One recorded sample s added to the per-voxel FP64 sums of s and s^2 (the
-// record mode of pass YZ does the same inside the sweep).
+// One recorded sample s added to the per-voxel sums of s and s^2 (FP64, or
+// double-float pairs for FP32 samples), with the arithmetic of the record
+// mode of pass YZ, which does the same inside the sweep.
+__device__ __forceinline__ void add_moment(const double* s, double* s1, double* s2, size_t i) {
+  const double x = s[i];
+  s1[i] += x;
+  s2[i] = fma(x, x, s2[i]);
+}
+__device__ __forceinline__ void add_moment(const float* s, double* s1, double* s2, size_t i) {
+  const float x = s[i];
+  float2* p1 = reinterpret_cast<float2*>(s1) + i;
+  float2* p2 = reinterpret_cast<float2*>(s2) + i;
+  float2 u = *p1, w = *p2;
+  df_add(u.x, u.y, x, 0.f);
+  const float p = __fmul_rn(x, x);
+  df_add(w.x, w.y, p, fmaf(x, x, -p));
+  *p1 = u;
+  *p2 = w;
+}
 template <typename T>
 __global__ void moments_kernel(const T* __restrict__ s, double* __restrict__ s1, double* __restrict__ s2, size_t M) {
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < M; i += size_t(gridDim.x) * blockDim.x) {
-    const double x = double(s[i]);
-    s1[i] += x;
-    s2[i] = fma(x, x, s2[i]);
-  }
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < M; i += size_t(gridDim.x) * blockDim.x)
+    add_moment(s, s1, s2, i);
 }
 
 // Efficiency analysis of a recorded P(k) trace (Sec. 4, statistical

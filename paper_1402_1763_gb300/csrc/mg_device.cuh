@@ -46,6 +46,32 @@ __device__ __forceinline__ void stc(typename VT<T>::c2* p, cx<T> a) {
 __device__ __forceinline__ double msg_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float msg_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 
+// Double-float sums (hi, lo) of FP32 values for the recorded samples: the
+// exact sum of (hi, lo) and q is hi + lo + q; TwoSum (Knuth) gives s + e =
+// hi + q exactly, the error joins lo, and Fast2Sum renormalises so |lo| <=
+// ulp(hi)/2.  Relative accuracy about 2^-44 over any number of additions.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float q, float qe) {
+  const float s = hi + q;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (q - bp);
+  const float t = lo + (e + qe);
+  hi = s + t;
+  lo = t - (hi - s);
+}
+// (h0, l0) += x0 and (h1, l1) += x1
+__device__ __forceinline__ void df_add_sample(float& h0, float& l0, float& h1, float& l1, float x0, float x1) {
+  df_add(h0, l0, x0, 0.f);
+  df_add(h1, l1, x1, 0.f);
+}
+// (h0, l0) += x0^2 and (h1, l1) += x1^2, each square split exactly into
+// x * x and its rounding error fma(x, x, -x * x) (the product rounded on its
+// own: __fmul_rn is never contracted into the following addition)
+__device__ __forceinline__ void df_add_square(float& h0, float& l0, float& h1, float& l1, float x0, float x1) {
+  const float p0 = __fmul_rn(x0, x0), p1 = __fmul_rn(x1, x1);
+  df_add(h0, l0, p0, fmaf(x0, x0, -p0));
+  df_add(h1, l1, p1, fmaf(x1, x1, -p1));
+}
+
 // Modes of pass YZ (mg_pass_yz.cuh).
 enum PassYZMode : int {
   kModeSweep = 0,        // inverse -> messenger draw -> forward (the hot path)
@@ -91,8 +117,9 @@ struct ChainDev {
   const typename VT<T>::c2* nyq2;
   const T* wloss;                     // [n][n][n/2+1] loss weight per stored mode
   T* dd;                              // [M] sum of lam_t over the adjoint sweeps (observed rows)
-  double* s1;                         // [M] sum of the recorded samples of s (record_every > 0)
-  double* s2;                         // [M] sum of their squares
+  double* s1;                         // [M] sum of the recorded samples of s (record_every > 0):
+                                      // FP64, or for FP32 chains a (hi, lo) float pair
+  double* s2;                         // [M] sum of their squares, the same way
   T tau;
   int B;
 };

@@ -86,23 +86,38 @@ __device__ __forceinline__ void add4(double* p, cx<double> a, cx<double> b) {
   q[1] = v;
 }
 
-// s1[0..3] += x, s2[0..3] += x^2 in FP64 for the four voxels x = (a.re,
-// a.im, b.re, b.im) (s1, s2 32-byte aligned).  The same arithmetic as
+// The sums of recorded samples: s1[0..3] += x, s2[0..3] += x^2 for the four
+// voxels x = (a.re, a.im, b.re, b.im), with the arithmetic of
 // moments_kernel, so fused and separate accumulation agree bit for bit.
-template <typename T>
-__device__ __forceinline__ void add_moments(double* s1, double* s2, cx<T> a, cx<T> b) {
+// FP64 samples: FP64 sums (s1, s2 32-byte aligned).
+__device__ __forceinline__ void add_moments(double* s1, double* s2, cx<double> a, cx<double> b) {
   double2* p1 = reinterpret_cast<double2*>(s1);
   double2* p2 = reinterpret_cast<double2*>(s2);
-  const double x0 = double(a.re), x1 = double(a.im), x2 = double(b.re), x3 = double(b.im);
   double2 u = p1[0], v = p1[1], w = p2[0], z = p2[1];
-  u.x += x0;
-  u.y += x1;
-  v.x += x2;
-  v.y += x3;
-  w.x = fma(x0, x0, w.x);
-  w.y = fma(x1, x1, w.y);
-  z.x = fma(x2, x2, z.x);
-  z.y = fma(x3, x3, z.y);
+  u.x += a.re;
+  u.y += a.im;
+  v.x += b.re;
+  v.y += b.im;
+  w.x = fma(a.re, a.re, w.x);
+  w.y = fma(a.im, a.im, w.y);
+  z.x = fma(b.re, b.re, z.x);
+  z.y = fma(b.im, b.im, z.y);
+  p1[0] = u;
+  p1[1] = v;
+  p2[0] = w;
+  p2[1] = z;
+}
+// FP32 samples: each sum a double-float (hi, lo) pair of floats in the same
+// 8 bytes (FP32 arithmetic only; GB300's FP64 rate is a small fraction of its
+// FP32 rate).
+__device__ __forceinline__ void add_moments(double* s1, double* s2, cx<float> a, cx<float> b) {
+  float4* p1 = reinterpret_cast<float4*>(s1);
+  float4* p2 = reinterpret_cast<float4*>(s2);
+  float4 u = p1[0], v = p1[1], w = p2[0], z = p2[1];  // (hi, lo) of two voxels each
+  df_add_sample(u.x, u.y, u.z, u.w, a.re, a.im);
+  df_add_sample(v.x, v.y, v.z, v.w, b.re, b.im);
+  df_add_square(w.x, w.y, w.z, w.w, a.re, a.im);
+  df_add_square(z.x, z.y, z.z, z.w, b.re, b.im);
   p1[0] = u;
   p1[1] = v;
   p2[0] = w;

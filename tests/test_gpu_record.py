@@ -14,6 +14,8 @@ samples (numpy mean and var with ddof = 1 of the same draws):
 * The persistent schedule (the samples added right after each sweep).
 * Alternating plain and mixing sweeps (both sweep kinds carry the record).
 * set_s with a sample pending adds the old state first.
+* The sums formed inside the sweep and by the separate pass agree bit for bit
+  (FP64 sums, and the double-float pairs of FP32 samples).
 """
 import numpy as np
 import pytest
@@ -113,3 +115,19 @@ def test_set_s_adds_the_pending_sample_first():
         g.set_s(0, np.zeros(m.shape))
         st = g.read_stats(0, maps=True)
     check(st, xs, 1e-12)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_fused_and_separate_sums_agree_bit_for_bit(precision):
+    need_gpu()
+    m = mockgen.make_mock(24, seed=76, n_bins=6, sigma_n=0.3)
+    with gpu_sampler(m, 6, 10, precision, record_every=1) as a, \
+            gpu_sampler(m, 6, 10, precision, record_every=1) as b:
+        for _ in range(6):
+            a.sweep(1)
+            a.read_stats(0, maps=True)  # every sample added by the separate pass
+        b.sweep(6)  # samples 1..5 added inside the next sweep, 6 by the read
+        sa, sb = a.read_stats(0, maps=True), b.read_stats(0, maps=True)
+    assert sa["records"] == sb["records"] == 6
+    np.testing.assert_array_equal(sa["mean"], sb["mean"])
+    np.testing.assert_array_equal(sa["var"], sb["var"])
