@@ -951,8 +951,10 @@ mg_status accumulate_now(mg_ctx* c) {
     }
     const LaunchArgs<T> a = one_chain_args<T>(*sc, i, static_cast<const ChainDev<T>*>(ch.rec_desc->p));
     MG_CUDA(c, launch_pass_yz<T>(sc->n, sc->C, kModeMaterialize, a, c->stream));
+    int P, Q;
+    split_of(g.n, &P, &Q);
     moments_kernel<T><<<1024, 256, 0, c->stream>>>(s, static_cast<double*>(ch.s1->p), static_cast<double*>(ch.s2->p),
-                                                   g.M);
+                                                   g.n, P, Q);
     MG_CUDA(c, cudaGetLastError());
   }
   return MG_OK;
@@ -1524,15 +1526,24 @@ mg_status mg_read_stats(mg_ctx* c, int32_t chain, mg_stats* out) {
     if (out->var) widen(out->var, g.M);
   }
   if (!s1.empty()) {
-    // mean = S1 / n, var = (S2 - S1 mean) / (n - 1) over the n recorded samples
+    // mean = S1 / n, var = (S2 - S1 mean) / (n - 1) over the n recorded
+    // samples, from the sums' row-slot order (sums_index) to [x][y][z]
+    std::vector<double> s2;
+    if (out->var) s2.assign(out->var, out->var + g.M);
     const double n_rec = double(c->records);
     const double inv_n = c->records > 0 ? 1.0 / n_rec : 0.0;
     const double inv_n1 = c->records > 1 ? 1.0 / (n_rec - 1.0) : 0.0;
-    for (size_t i = 0; i < g.M; ++i) {
-      const double mu = s1[i] * inv_n;
-      if (out->mean) out->mean[i] = mu;
-      if (out->var) out->var[i] = std::max(0.0, (out->var[i] - s1[i] * mu) * inv_n1);
-    }
+    int P, Q;
+    split_of(g.n, &P, &Q);
+    size_t i = 0;
+    for (int x = 0; x < g.n; ++x)
+      for (int y = 0; y < g.n; ++y)
+        for (int z = 0; z < g.n; ++z, ++i) {
+          const size_t j = sums_index(g.n, P, Q, x, y, z);
+          const double mu = s1[j] * inv_n;
+          if (out->mean) out->mean[i] = mu;
+          if (out->var) out->var[i] = std::max(0.0, (s2[j] - s1[j] * mu) * inv_n1);
+        }
   }
   return check_status(c);
 }

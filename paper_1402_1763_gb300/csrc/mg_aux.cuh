@@ -371,13 +371,11 @@ __global__ void sweep_bump_kernel(uint32_t* sweep_ctr) { atomicAdd(sweep_ctr, 1u
 // One recorded sample s added to the per-voxel sums of s and s^2 (FP64, or
 // double-float pairs for FP32 samples), with the arithmetic of the record
 // mode of pass YZ, which does the same inside the sweep.
-__device__ __forceinline__ void add_moment(const double* s, double* s1, double* s2, size_t i) {
-  const double x = s[i];
+__device__ __forceinline__ void add_moment(double x, double* s1, double* s2, size_t i) {
   s1[i] += x;
   s2[i] = fma(x, x, s2[i]);
 }
-__device__ __forceinline__ void add_moment(const float* s, double* s1, double* s2, size_t i) {
-  const float x = s[i];
+__device__ __forceinline__ void add_moment(float x, double* s1, double* s2, size_t i) {
   float2* p1 = reinterpret_cast<float2*>(s1) + i;
   float2* p2 = reinterpret_cast<float2*>(s2) + i;
   float2 u = *p1, w = *p2;
@@ -387,10 +385,16 @@ __device__ __forceinline__ void add_moment(const float* s, double* s1, double* s
   *p1 = u;
   *p2 = w;
 }
+// s: the materialised field in natural [x][y][z] order; the sums in the
+// order of sums_index.
 template <typename T>
-__global__ void moments_kernel(const T* __restrict__ s, double* __restrict__ s1, double* __restrict__ s2, size_t M) {
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < M; i += size_t(gridDim.x) * blockDim.x)
-    add_moment(s, s1, s2, i);
+__global__ void moments_kernel(const T* __restrict__ s, double* __restrict__ s1, double* __restrict__ s2, int n,
+                               int P, int Q) {
+  const size_t M = size_t(n) * n * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < M; i += size_t(gridDim.x) * blockDim.x) {
+    const int z = int(i % n), y = int((i / n) % n), x = int(i / (size_t(n) * n));
+    add_moment(s[i], s1, s2, sums_index(n, P, Q, x, y, z));
+  }
 }
 
 // Efficiency analysis of a recorded P(k) trace (Sec. 4, statistical

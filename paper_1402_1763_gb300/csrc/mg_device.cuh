@@ -72,6 +72,16 @@ __device__ __forceinline__ void df_add_square(float& h0, float& l0, float& h1, f
   df_add(h1, l1, p1, fmaf(x1, x1, -p1));
 }
 
+// Position of voxel (x, y, z) of an n^3 grid (n = P Q) in the sums of the
+// recorded samples: [x][z/4][slot][z%4] with slot = (y mod P) Q + y div P,
+// the order in which pass YZ's messenger stage visits the rows (consecutive
+// lanes take consecutive slots), so a warp's accesses of four voxels each are
+// one contiguous block.
+__host__ __device__ inline size_t sums_index(int n, int P, int Q, int x, int y, int z) {
+  const int slot = (y % P) * Q + y / P;
+  return ((size_t(x) * size_t(n / 4) + size_t(z / 4)) * size_t(n) + size_t(slot)) * 4 + size_t(z % 4);
+}
+
 // Modes of pass YZ (mg_pass_yz.cuh).
 enum PassYZMode : int {
   kModeSweep = 0,        // inverse -> messenger draw -> forward (the hot path)

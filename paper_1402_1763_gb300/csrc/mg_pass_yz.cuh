@@ -488,8 +488,12 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
       } else {
         if constexpr (MODE == kModeSweepRecord) {
           // the incoming state is a recorded sample: its s (exactly what the
-          // materialise pass writes) goes into the FP64 sums of s and s^2
-          if (rec) add_moments(cd.s1 + i0, cd.s2 + i0, Z0[q], Z1[q]);
+          // materialise pass writes) goes into the sums of s and s^2, stored
+          // in row-slot order so the warp's accesses are contiguous
+          if (rec) {
+            const size_t j = ((size_t(x) * (N / 4) + size_t(z0 / 4)) * N + size_t(sg)) * 4;  // sums_index
+            add_moments(cd.s1 + j, cd.s2 + j, Z0[q], Z1[q]);
+          }
         }
         const u32x4 w = philox4x32_10(uint32_t(i0 >> 2), sweep, cid, kStreamMessenger, k0, k1);
         T g0, g1, g2, g3;
