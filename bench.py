@@ -268,7 +268,7 @@ def run_other_workload(args):
                     batched_fp32_over_fp64=res[32][0] / res[64][0])
     elif args.workload == "record-256":
         # full-rate posterior summaries: the 256^3 workload (16 FP32 chains)
-        # with every sweep recorded (FP64 running mean and variance maps of s
+        # with every sweep recorded (the sums behind the mean and variance maps of s
         # and the P(k) trace of every chain), against the same sweeps unrecorded
         w = mockgen.workload(3)
         m = w.mocks[0]
