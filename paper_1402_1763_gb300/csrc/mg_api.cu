@@ -71,6 +71,15 @@ struct AdjWork {
   int K_cap = 0;  // checkpoints ck holds
   int B1 = 0;     // shells + 1 that acc and Psave hold
   std::shared_ptr<DevBuf> ck, scr, adj, wl64, wl, dd, ddw, acc, Psave, desc, sw;
+  cudaStream_t up = nullptr;  // the loss weights' upload, beside the forward sweeps
+  cudaEvent_t up_ev = nullptr;
+  AdjWork() = default;
+  AdjWork(const AdjWork&) = delete;
+  AdjWork& operator=(const AdjWork&) = delete;
+  ~AdjWork() {
+    if (up_ev) cudaEventDestroy(up_ev);
+    if (up) cudaStreamDestroy(up);
+  }
 };
 
 }  // namespace
@@ -797,6 +806,8 @@ mg_status adjoint_impl(mg_ctx* c, int chain, int K, const double* logP, const do
     MG_CUDA(c, e);
     w.sw = dalloc(sizeof(uint32_t), &e);
     MG_CUDA(c, e);
+    MG_CUDA(c, cudaStreamCreateWithFlags(&w.up, cudaStreamNonBlocking));
+    MG_CUDA(c, cudaEventCreateWithFlags(&w.up_ev, cudaEventDisableTiming));
     LaunchArgs<T> none;  // set the adjoint kernels' attributes (outside any capture)
     std::memset(&none, 0, sizeof(none));
     MG_CUDA(c, launch_pass_yz<T>(n, sc->C, 3, none, c->stream));
@@ -827,14 +838,13 @@ mg_status adjoint_impl(mg_ctx* c, int chain, int K, const double* logP, const do
   uint32_t* ctr = static_cast<uint32_t*>(c->d_sweep->p);
   const uint32_t* sw0 = static_cast<const uint32_t*>(w.sw->p);
 
-  // Host-to-device uploads first, while the stream holds no kernels (a copy
-  // from pageable memory waits for the stream): the loss weights, P =
-  // exp(logP) after saving the chain's P, and the four adjoint descriptors:
+  // Small host-to-device uploads first, while the stream holds no kernels (a
+  // copy from pageable memory waits for its stream): P = exp(logP) after
+  // saving the chain's P, and the four adjoint descriptors:
   //   [0] the chain, [1] pass YZ recomputing t, [2] pass X of the last sweep,
   //   [3] pass X of earlier sweeps, [4] the adjoint pass YZ.
-  MG_CUDA(c, cudaMemcpyAsync(w.wl64->p, wl_host, Mh * sizeof(double), cudaMemcpyHostToDevice, s));
-  adjoint_weights_kernel<T><<<1024, 256, 0, s>>>(static_cast<const double*>(w.wl64->p), n, static_cast<T*>(w.wl->p));
-  MG_CUDA(c, cudaGetLastError());
+  // The loss weights (n^2 (n/2+1) doubles) go up on a stream of their own
+  // once the forward sweeps are queued, so their staging overlaps them.
   MG_CUDA(c, cudaMemcpyAsync(w.Psave->p, ch.P->p, size_t(B1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
   std::vector<double> Pn(B1);
   for (int b = 0; b < B1; ++b) Pn[b] = std::exp(logP[b]);
@@ -881,6 +891,14 @@ mg_status adjoint_impl(mg_ctx* c, int chain, int K, const double* logP, const do
     MG_CUDA(c, cudaMemcpyAsync(ck_main(k), ch.main->p, main_b, cudaMemcpyDeviceToDevice, s));
     MG_CUDA(c, cudaMemcpyAsync(ck_nyq(k), ch.nyq->p, nyq_b, cudaMemcpyDeviceToDevice, s));
   }
+
+  // the loss weights, needed from the first adjoint sweep on
+  MG_CUDA(c, cudaMemcpyAsync(w.wl64->p, wl_host, Mh * sizeof(double), cudaMemcpyHostToDevice, w.up));
+  adjoint_weights_kernel<T><<<1024, 256, 0, w.up>>>(static_cast<const double*>(w.wl64->p), n,
+                                                     static_cast<T*>(w.wl->p));
+  MG_CUDA(c, cudaGetLastError());
+  MG_CUDA(c, cudaEventRecord(w.up_ev, w.up));
+  MG_CUDA(c, cudaStreamWaitEvent(s, w.up_ev, 0));
 
   // adjoint sweeps K .. 1
   double* grad = static_cast<double*>(w.acc->p);
