@@ -53,7 +53,7 @@ typedef enum {
   MG_ENUMERIC = 5,     /* a shell draw met sigma_b <= 0, X_b <= 0 or non-finite
                           values; that shell kept its previous P              */
   MG_ESTATE = 6,       /* call not valid in the context's current state       */
-  MG_EUNSUPPORTED = 7  /* valid request this build does not implement         */
+  MG_EUNSUPPORTED = 7  /* valid request the library does not implement        */
 } mg_status;
 
 typedef struct mg_ctx mg_ctx;
@@ -145,7 +145,7 @@ void mg_options_init(mg_options* opt);
  * (ignored where R = 0); at least one voxel observed.  k_edges: NULL or
  * n_bins+1 doubles.  The chains start at s = 0 and P = opt->P0.
  * Errors: MG_EINVAL for invalid arguments or data, MG_EUNSUPPORTED for grids
- * this build does not cover, MG_ENOMEM / MG_ECUDA.  *out is NULL on error. */
+ * the library does not cover, MG_ENOMEM / MG_ECUDA.  *out is NULL on error. */
 mg_status mg_init(mg_ctx** out, const mg_grid* grid, const double* N, const double* R,
                   const double* d, const double* k_edges, int32_t n_bins, uint64_t seed,
                   const mg_options* opt);
