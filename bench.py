@@ -273,8 +273,9 @@ def run_other_workload(args):
         w = mockgen.workload(3)
         m = w.mocks[0]
         res = {}
+        nc = args.chains
         for rec in (1, 0):
-            g = Sampler.single(m.n, m.L, m.N, m.R, m.d, m.n_bins, 3, precision=32, n_chains=16,
+            g = Sampler.single(m.n, m.L, m.N, m.R, m.d, m.n_bins, 3, precision=32, n_chains=nc,
                                record_every=rec, stream=stream.cuda_stream)
             g.sweep(args.warmup)
             g.sync()
@@ -284,8 +285,9 @@ def run_other_workload(args):
             torch.cuda.synchronize()
             res[rec] = ev[0].elapsed_time(ev[1]) / args.steps
             g.close()
-        line.update(value=16 * m.n ** 3 / (res[1] * 1e-3), ms_per_step=res[1], dtype="f32",
-                    config={"workload": w.name + "-record-every-sweep", "chains": 16},
+        line.update(value=nc * m.n ** 3 / (res[1] * 1e-3), ms_per_step=res[1], dtype="f32",
+                    config={"workload": w.name.replace("16chains", f"{nc}chains") + "-record-every-sweep",
+                            "chains": nc},
                     ms_per_step_unrecorded=res[0])
     elif args.workload == "fp64-128holes":
         w = mockgen.workload(2)
@@ -411,6 +413,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chains", type=int, default=16, help="chains of the record-256 workload")
     ap.add_argument("--workload", default="256-fp32-16chains",
                     choices=["256-fp32-16chains", "batch-48chains", "adjoint-128", "fp64-128holes",
                              "fp32-vs-fp64-128", "record-256", "mixing-256", "mixing-acf", "precision-256"])
