@@ -53,7 +53,10 @@ typedef enum {
   MG_ENUMERIC = 5,     /* a shell draw met sigma_b <= 0, X_b <= 0 or non-finite
                           values; that shell kept its previous P              */
   MG_ESTATE = 6,       /* call not valid in the context's current state       */
-  MG_EUNSUPPORTED = 7  /* valid request the library does not implement        */
+  MG_EUNSUPPORTED = 7, /* valid request the library does not implement        */
+  MG_EBOUNDS = 8       /* bounds-checked build only (mg_build_flags): a kernel
+                          met an index outside its buffer; the access was
+                          skipped                                             */
 } mg_status;
 
 typedef struct mg_ctx mg_ctx;
@@ -324,14 +327,43 @@ mg_status mg_philox(uint64_t seed, uint32_t ctr0, uint32_t ctr1, uint32_t ctr2, 
  *          (w = 2 for 0 < kz < n/2, 1 on the kz = 0 and n/2 planes; DC excluded).
  *   nmodes_out: device, n_bins+1 doubles (sum of w), or NULL.
  *   stream: cudaStream_t or NULL; the call is asynchronous on it.
+ * Every sum is formed in a fixed order, so repeated calls on the same input
+ * return the same bits.
  * Scratch: a fixed file-scope device array of 256 x 255 x 2 doubles (1 MiB)
  * that every GPU loading the library holds until exit; n_bins > 254 does not
- * fit and returns MG_EINVAL (mg_last_error(NULL) says why).  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) — make
- * that first call before any stream capture.  All calls share the array:
- * calls that overlap on the GPU (other streams, other threads) race. */
+ * fit and returns MG_EINVAL.  The first call in a CUDA context (per device,
+ * and again after cudaDeviceReset) looks up the array's device address
+ * (cudaGetSymbolAddress) — make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (other streams,
+ * other threads) race.  Errors: MG_EINVAL for bad arguments; MG_ECUDA if a
+ * CUDA error from earlier work is already pending (nothing is launched), if
+ * the address lookup fails (a later call retries it) or if a launch fails.
+ * mg_last_error(NULL) gives the reason on this thread. */
 mg_status mg_shell_sums_noalloc(const void* s_hat, int32_t precision, int32_t n, int32_t n_bins,
                                 double* sigma_out, double* nmodes_out, void* stream);
+
+/* Failure-detection hook, for tests of the error paths without a GPU fault
+ * (the paper has no counterpart).  The after_calls-th checked CUDA runtime
+ * call that context c makes from now on (1 = the next) is not made: it
+ * reports cudaErrorUnknown, as a failing call would, so the library call that
+ * made it returns MG_ECUDA, which is then sticky on c (mg_last_error says the
+ * failure was injected).  0 disarms.  Nothing runs on the device because of
+ * it.  MG_EINVAL for a null context or after_calls < 0. */
+mg_status mg_inject_cuda_error(mg_ctx* c, int32_t after_calls);
+
+/* FP64 fused multiply-add throughput of the current device in GFLOP/s
+ * (2 flops per FMA), measured with CUDA events over three launches of a
+ * kernel of independent FMA chains (best of three): the roofline denominator
+ * of the FP64 sweep, which is bound by the FP64 pipe.  stream: cudaStream_t
+ * or NULL.  Allocates and frees a small buffer; synchronises.  MG_EINVAL for
+ * a null output, MG_ECUDA if a CUDA call fails. */
+mg_status mg_fp64_fma_peak(double* gflops, void* stream);
+
+/* How the library was built: MG_BUILD_CHECKED is set in the bounds-checked
+ * build (every device index taken from a host table is checked before use; a
+ * violation is skipped and reported as MG_EBOUNDS; grid sizes n <= 32 only). */
+#define MG_BUILD_CHECKED 1
+int32_t mg_build_flags(void);
 
 #ifdef __cplusplus
 }

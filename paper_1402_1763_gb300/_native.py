@@ -7,15 +7,18 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-MG_OK, MG_EINVAL, MG_ENOMEM, MG_ECUDA, MG_ETIMEOUT, MG_ENUMERIC, MG_ESTATE, MG_EUNSUPPORTED = range(8)
+MG_OK, MG_EINVAL, MG_ENOMEM, MG_ECUDA, MG_ETIMEOUT, MG_ENUMERIC, MG_ESTATE, MG_EUNSUPPORTED, MG_EBOUNDS = range(9)
 _NAMES = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ETIMEOUT",
-          5: "MG_ENUMERIC", 6: "MG_ESTATE", 7: "MG_EUNSUPPORTED"}
+          5: "MG_ENUMERIC", 6: "MG_ESTATE", 7: "MG_EUNSUPPORTED", 8: "MG_EBOUNDS"}
+MG_BUILD_CHECKED = 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def library_path() -> str:
-    return os.path.join(_HERE, "_lib", "libmg.so")
+    """The main library, or its bounds-checked build when MG_CHECKED=1."""
+    name = "libmg_checked.so" if os.environ.get("MG_CHECKED") == "1" else "libmg.so"
+    return os.path.join(_HERE, "_lib", name)
 
 
 class MgGrid(C.Structure):
@@ -93,6 +96,9 @@ def library():
         "mg_pk_quantiles": (C.c_int, [_P, C.c_int32, C.c_int32, _D, _D]),
         "mg_pk_rhat": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int64, _D]),
         "mg_read_pk_all": (C.c_int, [_P, _D]),
+        "mg_inject_cuda_error": (C.c_int, [_P, C.c_int32]),
+        "mg_build_flags": (C.c_int32, []),
+        "mg_fp64_fma_peak": (C.c_int, [_D, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -511,3 +517,19 @@ def mg_shell_sums_noalloc(s_hat_ptr: int, precision: int, n: int, n_bins: int, s
     _check(library().mg_shell_sums_noalloc(C.c_void_p(s_hat_ptr), int(precision), int(n), int(n_bins),
                                            C.c_void_p(sigma_ptr), C.c_void_p(nmodes_ptr or None),
                                            C.c_void_p(stream or None)))
+
+
+def mg_inject_cuda_error(ctx, after_calls: int):
+    """Fake the failure of the after_calls-th checked CUDA call of ctx (see include/mg.h)."""
+    _check(library().mg_inject_cuda_error(ctx, int(after_calls)), ctx)
+
+
+def mg_build_flags() -> int:
+    return int(library().mg_build_flags())
+
+
+def mg_fp64_fma_peak(stream: int = 0) -> float:
+    """Measured FP64 FMA throughput of the current device, GFLOP/s (see include/mg.h)."""
+    out = C.c_double(0.0)
+    _check(library().mg_fp64_fma_peak(C.byref(out), C.c_void_p(stream or None)))
+    return out.value

@@ -42,6 +42,7 @@ struct Group {
   size_t M = 0;
   std::vector<long long> n_b;  // B+1
   std::shared_ptr<DevBuf> bc, bin_of_m2, n_b_dev, gamma, row_info, bc_rows;
+  uint32_t bc_rows_len = 0;  // complex entries in bc_rows
 };
 
 struct Chain {
@@ -118,6 +119,7 @@ struct mg_ctx {
   std::shared_ptr<DevBuf> persist_ctr;
   int persist_grid = 0;
   long long timeout = 0;
+  int fault_in = 0;  // mg_inject_cuda_error: checked CUDA calls left until a faked failure (0: off)
 };
 
 namespace {
@@ -128,16 +130,26 @@ mg_status fail(mg_ctx* c, mg_status s, const std::string& msg) {
   g_create_error = msg;
   if (c) {
     c->err = msg;
-    if (s == MG_ECUDA || s == MG_ENUMERIC || s == MG_ETIMEOUT) c->sticky = s;
+    if (s == MG_ECUDA || s == MG_ENUMERIC || s == MG_ETIMEOUT || s == MG_EBOUNDS) c->sticky = s;
   }
   return s;
 }
 
-#define MG_CUDA(ctx, call)                                                        \
-  do {                                                                            \
-    cudaError_t e_ = (call);                                                      \
-    if (e_ != cudaSuccess)                                                        \
-      return fail(ctx, MG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+// Host-side fault injection (mg_inject_cuda_error): the checked CUDA call that
+// brings the context's countdown to zero is not made and reports
+// cudaErrorUnknown instead, as a failing call would.
+bool fake_cuda_fault(mg_ctx* c) {
+  if (!c || c->fault_in <= 0) return false;
+  return --c->fault_in == 0;
+}
+
+#define MG_CUDA(ctx, call)                                                                  \
+  do {                                                                                      \
+    const bool fake_ = fake_cuda_fault(ctx);                                                \
+    cudaError_t e_ = fake_ ? cudaErrorUnknown : (call);                                     \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(ctx, MG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_) +       \
+                                     (fake_ ? " (injected by mg_inject_cuda_error)" : "")); \
   } while (0)
 
 std::shared_ptr<DevBuf> dalloc(size_t bytes, cudaError_t* err) {
@@ -151,7 +163,7 @@ std::shared_ptr<DevBuf> dalloc(size_t bytes, cudaError_t* err) {
 bool is_supported_n(int n) {
   static const int ok[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256};
   for (int v : ok)
-    if (v == n) return true;
+    if (v == n) return n <= MG_MAX_N;
   return false;
 }
 
@@ -273,6 +285,8 @@ mg_status upload_descriptors(mg_ctx* c) {
       d.s2 = ch.s2 ? static_cast<double*>(ch.s2->p) : nullptr;
       d.s_out = nullptr;
       d.s_in = nullptr;
+      d.status = static_cast<int*>(c->d_status->p);
+      d.bc_rows_len = g.bc_rows_len;
       d.tau = T(g.tau);
       d.B = g.B;
     }
@@ -942,6 +956,8 @@ mg_status check_status(mg_ctx* c) {
   int st = 0;
   MG_CUDA(c, cudaMemcpyAsync(&st, c->d_status->p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (st & kStBounds)
+    return fail(c, MG_EBOUNDS, "checked build: a kernel met an index outside its buffer (the access was skipped)");
   if (st & kStTimeout) return fail(c, MG_ETIMEOUT, "a device-side wait ran out of its budget");
   if (st & kStNumeric)
     return fail(c, MG_ENUMERIC, "a shell draw met a non-positive or non-finite sum; the shell kept its P");
@@ -1131,7 +1147,8 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
       g.row_info = dalloc(ri.size() * sizeof(uint32_t), &e);
       MG_CUDA(c, e);
       MG_CUDA(c, cudaMemcpy(g.row_info->p, ri.data(), ri.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-      g.bc_rows = dalloc(size_t(std::max<uint32_t>(off, 4)) * sizeof(V2), &e);
+      g.bc_rows_len = std::max<uint32_t>(off, 4);
+      g.bc_rows = dalloc(size_t(g.bc_rows_len) * sizeof(V2), &e);
       MG_CUDA(c, e);
       pack_rows_kernel<T><<<1024, 256, 0, c->stream>>>(static_cast<const V2*>(g.bc->p),
                                                        static_cast<const uint2*>(g.row_info->p), n,
@@ -1801,6 +1818,20 @@ mg_status mg_sync(mg_ctx* c) {
   if (!c) return MG_EINVAL;
   MG_CUDA(c, cudaStreamSynchronize(c->stream));
   return check_status(c);
+}
+
+mg_status mg_inject_cuda_error(mg_ctx* c, int32_t after_calls) {
+  if (!c || after_calls < 0) return MG_EINVAL;
+  c->fault_in = after_calls;
+  return MG_OK;
+}
+
+int32_t mg_build_flags(void) {
+#ifdef MG_CHECKED
+  return MG_BUILD_CHECKED;
+#else
+  return 0;
+#endif
 }
 
 const char* mg_last_error(const mg_ctx* c) {

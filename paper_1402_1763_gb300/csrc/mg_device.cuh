@@ -94,7 +94,23 @@ enum PassYZMode : int {
 };
 
 // Device status bits (sticky on the context once read by the host).
-enum : int { kStNumeric = 1, kStTimeout = 2, kStBadInput = 4, kStNoObserved = 8 };
+enum : int { kStNumeric = 1, kStTimeout = 2, kStBadInput = 4, kStNoObserved = 8, kStBounds = 16 };
+
+// Largest grid size the kernels are instantiated for (the bounds-checked build
+// compiles the small sizes only).
+#ifndef MG_MAX_N
+#define MG_MAX_N 256
+#endif
+
+// Bounds-checked build (-DMG_CHECKED): every device index that comes from a
+// table built on the host, not from compile-time loop limits over the grid and
+// the tile, is compared with its buffer before use.  A violation sets
+// kStBounds in the context's status word (reported as MG_EBOUNDS, sticky) and
+// the access is skipped; nothing traps.  Without MG_CHECKED the checks are not
+// compiled.
+__device__ __forceinline__ void flag_bounds(int* status) {
+  if (status) atomicOr(status, kStBounds);
+}
 
 // One chain as the sweep kernels see it.  State layout (per chain):
 //   main[x][ky][kz]  kz in [0, n/2)  complex: the spectrum with x still in
@@ -130,6 +146,8 @@ struct ChainDev {
   double* s1;                         // [M] sum of the recorded samples of s (record_every > 0):
                                       // FP64, or for FP32 chains a (hi, lo) float pair
   double* s2;                         // [M] sum of their squares, the same way
+  int* status;                        // the context's device status word
+  uint32_t bc_rows_len;               // complex entries in bc_rows
   T tau;
   int B;
 };

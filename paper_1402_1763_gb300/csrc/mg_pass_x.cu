@@ -73,12 +73,24 @@ cudaError_t launch_pass_x(int n, int mode, const LaunchArgs<T>& args, int B_max,
     MG_CASE(16)
     MG_CASE(24)
     MG_CASE(32)
+#if MG_MAX_N >= 48
     MG_CASE(48)
+#endif
+#if MG_MAX_N >= 64
     MG_CASE(64)
+#endif
+#if MG_MAX_N >= 96
     MG_CASE(96)
+#endif
+#if MG_MAX_N >= 128
     MG_CASE(128)
+#endif
+#if MG_MAX_N >= 192
     MG_CASE(192)
+#endif
+#if MG_MAX_N >= 256
     MG_CASE(256)
+#endif
 #undef MG_CASE
     default:
       return cudaErrorInvalidValue;

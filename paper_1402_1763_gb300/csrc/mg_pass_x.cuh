@@ -100,7 +100,16 @@ __device__ __forceinline__ int mode_bin(int kx, int ky, int kz, const ChainDev<T
   const int mx = kx <= H ? kx : kx - N;
   const int my = ky <= H ? ky : ky - N;
   const int m2 = mx * mx + my * my + kz * kz;
-  return m2 == 0 ? -1 : int(__ldg(cd.bin_of_m2 + m2));
+  int b = m2 == 0 ? -1 : int(__ldg(cd.bin_of_m2 + m2));
+#ifdef MG_CHECKED
+  // shell ids come from a host table; the per-warp sums and the coefficients
+  // hold B + 1 shells
+  if (b > cd.B) {
+    flag_bounds(cd.status);
+    b = -1;  // contributes nothing, coefficients of the DC entry
+  }
+#endif
+  return b;
 }
 template <typename T, int N>
 __device__ __forceinline__ int mode_shell(int kx, int ky, int kz, const ChainDev<T>& cd, cx<T>& cf) {
@@ -225,8 +234,15 @@ __device__ __forceinline__ cx<T> adjoint_mode(cx<T> G, cx<T> Ft, int kx, int ky,
   const int m2 = mx * mx + my * my + kz * kz;
   const bool edge = (kz == 0) || (kz == H);
   const T wd = edge ? T(1) : T(2);
-  const bool dc = (m2 == 0);
+  bool dc = (m2 == 0);
   bin = dc ? -1 : int(__ldg(cd.bin_of_m2 + m2));
+#ifdef MG_CHECKED
+  if (bin > cd.B) {  // shell ids come from a host table (see mode_bin)
+    flag_bounds(cd.status);
+    bin = -1;
+    dc = true;
+  }
+#endif
   const cx<T> cf = ldc<T>(cd.coef + (dc ? cd.B + 1 : bin));
   loss = T(0);
   if constexpr (MODE == kXAdjTop) {

@@ -430,6 +430,15 @@ __device__ __forceinline__ void pass_yz_unit(const LaunchArgs<T>& a, int unit, u
       lo = ri.y & 0xffffu;
       hi = ri.y >> 16;
       brow = cd.bc_rows + ri.x;
+#ifdef MG_CHECKED
+      // the row's observed range and its offset come from a host table: the
+      // range must lie in the row, 4-voxel aligned, and inside bc_rows
+      if (!(lo <= hi && hi <= uint32_t(N) && lo % 4 == 0 && hi % 4 == 0 &&
+            size_t(ri.x) + (hi - lo) <= size_t(cd.bc_rows_len))) {
+        flag_bounds(cd.status);
+        lo = hi = 0;  // treated as unobserved: no load
+      }
+#endif
     }
     auto load_group = [&](int z, cx<T>* out) {
       if (uint32_t(z) >= lo && uint32_t(z) < hi) {

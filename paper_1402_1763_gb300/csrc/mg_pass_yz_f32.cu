@@ -13,16 +13,36 @@ cudaError_t launch_pass_yz<float>(int n, int C, int mode, const LaunchArgs<float
   MG_CASE(16, 1)
   MG_CASE(24, 1)
   MG_CASE(32, 1)
+#if MG_MAX_N >= 48
   MG_CASE(48, 1)
+#endif
+#if MG_MAX_N >= 64
   MG_CASE(64, 1)
+#endif
+#if MG_MAX_N >= 96
   MG_CASE(96, 1)
+#endif
+#if MG_MAX_N >= 128
   MG_CASE(128, 1)
+#endif
+#if MG_MAX_N >= 128
   MG_CASE(128, 2)
+#endif
+#if MG_MAX_N >= 192
   MG_CASE(192, 1)
+#endif
+#if MG_MAX_N >= 192
   MG_CASE(192, 2)
+#endif
+#if MG_MAX_N >= 256
   MG_CASE(256, 2)
+#endif
+#if MG_MAX_N >= 256
   MG_CASE(256, 4)
+#endif
+#if MG_MAX_N >= 256
   MG_CASE(256, 8)
+#endif
 #undef MG_CASE
   return cudaErrorInvalidValue;
 }

@@ -120,10 +120,18 @@ __device__ __forceinline__ void run_yz(const PersistArgs<T>& a, int k, int local
     MG_P(16)
     MG_P(24)
     MG_P(32)
+#if MG_MAX_N >= 48
     MG_P(48)
+#endif
+#if MG_MAX_N >= 64
     MG_P(64)
+#endif
+#if MG_MAX_N >= 96
     MG_P(96)
+#endif
+#if MG_MAX_N >= 128
     MG_P(128)
+#endif
 #undef MG_P
     default:
       break;
@@ -140,10 +148,18 @@ __device__ __forceinline__ void run_x(const PersistArgs<T>& a, int k, int local,
     MG_P(16)
     MG_P(24)
     MG_P(32)
+#if MG_MAX_N >= 48
     MG_P(48)
+#endif
+#if MG_MAX_N >= 64
     MG_P(64)
+#endif
+#if MG_MAX_N >= 96
     MG_P(96)
+#endif
+#if MG_MAX_N >= 128
     MG_P(128)
+#endif
 #undef MG_P
     default:
       break;
@@ -202,10 +218,18 @@ size_t smem_needed(int n, int B_max) {
     MG_P(16)
     MG_P(24)
     MG_P(32)
+#if MG_MAX_N >= 48
     MG_P(48)
+#endif
+#if MG_MAX_N >= 64
     MG_P(64)
+#endif
+#if MG_MAX_N >= 96
     MG_P(96)
+#endif
+#if MG_MAX_N >= 128
     MG_P(128)
+#endif
 #undef MG_P
     default:
       return 0;
@@ -214,7 +238,9 @@ size_t smem_needed(int n, int B_max) {
 
 }  // namespace
 
-bool persist_supports(int n) { return n == 16 || n == 24 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128; }
+bool persist_supports(int n) {
+  return n <= MG_MAX_N && (n == 16 || n == 24 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128);
+}
 
 template <typename T>
 size_t persist_smem(const PersistArgs<T>& a, int B_max) {

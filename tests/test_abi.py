@@ -34,6 +34,24 @@ def test_library_exports_every_declared_symbol(lib):
     assert not missing, missing
 
 
+def test_checked_build_exports_every_declared_symbol(lib):
+    """The bounds-checked variant (built beside the main library) has the same
+    entry points and reports itself through mg_build_flags."""
+    from paper_1402_1763_gb300 import build
+    chk = ctypes.CDLL(build.LIB_CHECKED)
+    missing = [n for n in declared_functions() if not hasattr(chk, n)]
+    assert not missing, missing
+    chk.mg_build_flags.restype = ctypes.c_int32
+    lib.mg_build_flags.restype = ctypes.c_int32
+    assert chk.mg_build_flags() == 1 and lib.mg_build_flags() == 0
+
+
+def test_fault_injection_hook_rejects_bad_arguments_without_gpu(lib):
+    from paper_1402_1763_gb300 import _native as nv
+    L = nv.library()
+    assert L.mg_inject_cuda_error(None, 1) == nv.MG_EINVAL
+
+
 def test_binding_mirrors_the_abi():
     import paper_1402_1763_gb300 as pkg
     missing = [n for n in declared_functions() if not hasattr(pkg, n)]
