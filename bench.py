@@ -133,51 +133,124 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def run_reference(args, rank):
-    """FP64 CPU oracle on this host: each step is one sweep of one chain of the
-    same 256^3 workload (a bounded sample of the 16-chain step)."""
-    if rank != 0:
-        return 0
+def _oracle_worker(conn, chain_id):
+    """One process of the CPU baseline: one oracle chain of the 256^3 workload
+    (its own chain id), one sweep per request; replies with the sweep's wall time."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import sampler
     m = mockgen.make_mock(N_GRID, seed=SEED, n_bins=N_BINS)
     prob = sampler.make_problem(m.shape, m.L, m.N, m.R, m.d, N_BINS)
-    ch = sampler.Chains(prob, seed=SEED, chain_ids=[0])
-    for _ in range(args.warmup):
+    ch = sampler.Chains(prob, seed=SEED, chain_ids=[chain_id])
+    conn.send("ready")
+    while True:
+        msg = conn.recv()
+        if msg != "sweep":
+            break
+        t0 = time.perf_counter()
         ch.sweep(1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ch.sweep(1)
-    dt = (time.perf_counter() - t0) / args.steps
-    v = N_GRID ** 3 / dt
+        conn.send(time.perf_counter() - t0)
+    conn.close()
+
+
+class OraclePool:
+    """The FP64 oracle on every host core: one independent chain per process
+    (the paper's independent-chains strategy, Sec. 3.4), each single-threaded.
+    Processes are started with spawn (safe after CUDA is initialised)."""
+
+    def __init__(self, cores: int):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.cores = cores
+        self.conns, self.procs = [], []
+        env_threads = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in env_threads:
+            os.environ[k] = "1"
+        try:
+            for c in range(cores):
+                a, b = ctx.Pipe()
+                p = ctx.Process(target=_oracle_worker, args=(b, c), daemon=True)
+                p.start()
+                self.conns.append(a)
+                self.procs.append(p)
+        finally:
+            for k, v in env_threads.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        for cn in self.conns:
+            assert cn.recv() == "ready"
+
+    def step(self) -> float:
+        """One sweep of every chain, all processes at once; wall seconds."""
+        t0 = time.perf_counter()
+        for cn in self.conns:
+            cn.send("sweep")
+        for cn in self.conns:
+            cn.recv()
+        return time.perf_counter() - t0
+
+    def close(self):
+        for cn in self.conns:
+            try:
+                cn.send("stop")
+            except (BrokenPipeError, OSError):
+                pass
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, rank):
+    """FP64 CPU oracle on this host's cores: each step is one sweep of one
+    chain per core of the same 256^3 workload (independent chains, a bounded
+    sample of the 16-chain step)."""
+    if rank != 0:
+        return 0
+    cores = host_cores()
+    pool = OraclePool(cores)
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        t = 0.0
+        for _ in range(args.steps):
+            t += pool.step()
+    finally:
+        pool.close()
+    dt = t / args.steps
+    v = cores * N_GRID ** 3 / dt
+    sample = (f"{cores} independent chains x 1 sweep of the 256^3 workload per step, one single-threaded "
+              "numpy FP64 process per core")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "1 chain x 1 sweep per step (of 16 chains)",
-                       "grid": N_GRID, "shells": N_BINS},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "1 chain x 1 sweep of the 256^3 workload per step; numpy FP64, "
-                                       "single-threaded"},
+            "config": {"workload": WORKLOAD, "sample": sample, "grid": N_GRID, "shells": N_BINS},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def cpu_baseline(seconds_budget=25.0):
-    """The oracle as it stands, one chain of the workload, single-threaded numpy."""
-    from oracle import sampler
-    m = mockgen.make_mock(N_GRID, seed=SEED, n_bins=N_BINS)
-    prob = sampler.make_problem(m.shape, m.L, m.N, m.R, m.d, N_BINS)
-    ch = sampler.Chains(prob, seed=SEED, chain_ids=[0])
-    t0 = time.perf_counter()
-    sweeps = 0
-    while sweeps < 1 or (time.perf_counter() - t0 < seconds_budget / 3 and sweeps < 3):
-        ch.sweep(1)
-        sweeps += 1
-    dt = (time.perf_counter() - t0) / sweeps
-    return {"value": N_GRID ** 3 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sweeps} sweep(s) of 1 chain of the 256^3 workload (of 16 per step); "
-                      "numpy FP64 single-threaded"}
+def cpu_baseline(sweeps=2):
+    """The oracle as it stands on every host core: one independent chain per
+    core, `sweeps` sweeps each (a bounded sample of the workload)."""
+    cores = host_cores()
+    pool = OraclePool(cores)
+    try:
+        t = sum(pool.step() for _ in range(sweeps))
+    finally:
+        pool.close()
+    dt = t / sweeps
+    return {"value": cores * N_GRID ** 3 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} independent chains (one single-threaded numpy FP64 process per core) x {sweeps} "
+                      "sweeps of the 256^3 workload"}
 
 
 def tau_int(x) -> float:
@@ -533,6 +606,23 @@ def main():
         s64.close()
         fp64 = {"value": M / (ms64 * 1e-3), "unit": UNIT, "ms_per_sweep": ms64,
                 "config": "plain FP64, 1 chain, same 256^3 data"}
+        # The FP64 sweep is bound by the FP64 pipe: its roofline is the FP64
+        # flops of one sweep (2 per DFMA, 1 per DADD / DMUL, counted by ncu on
+        # the same kernel build) over the sweep time, against the DFMA
+        # throughput measured live on this GPU.
+        from paper_1402_1763_gb300 import mg_fp64_fma_peak
+        peak64 = mg_fp64_fma_peak(stream.cuda_stream)
+        fp64["fp64_peak_gflops"] = peak64
+        fp64["fp64_peak_kind"] = "measured (DFMA microkernel, mg_fp64_fma_peak)"
+        flops64 = None
+        fp = os.path.join(ROOT, "profiles", "fp64_flops_256cubed_1chain.json")
+        if os.path.exists(fp):
+            with open(fp) as f:
+                fj = json.load(f)
+            if fj.get("source_hash") == kernel_source_hash():
+                flops64 = fj["fp64_flops_per_sweep"]
+        fp64["fp64_flops_per_sweep"] = flops64
+        fp64["fp64_frac"] = (flops64 / (ms64 * 1e-3) / 1e9 / peak64) if flops64 else None
 
     # comparison only: the library transforms (cuFFT via torch.fft) of one
     # sweep's work, one forward R2C and one inverse C2R 3D FFT per chain, with
