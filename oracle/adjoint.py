@@ -59,7 +59,7 @@ def chain_loss(prob, logP, d, w, K, seed, chain_id=0, sweep0=0, s0=None):
     s = torch.zeros(prob.shape, dtype=torch.float64) if s0 is None else _t(s0)
     s_hat = None
     for k in range(K):
-        g, z0, z1, _, _ = sampler.sweep_draws(prob.shape, seed, sweep0 + k, [chain_id])
+        g, z0, z1 = sampler.sweep_draws(prob.shape, seed, sweep0 + k, [chain_id])
         s, s_hat = sweep_fixed_P(prob, s, logP, d, _t(g[0]), z0[0], z1[0])
     return (_t(w) * (s_hat.real ** 2 + s_hat.imag ** 2)).sum()
 

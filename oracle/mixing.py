@@ -161,8 +161,7 @@ class MixingChains(sp.Chains):
 
     def sweep(self, n: int = 1):
         for _ in range(n):
-            g, z0, z1, _, _ = sp.sweep_draws(self.prob.shape, self.seed, self.sweeps_done,
-                                             self.chain_ids)
+            g, z0, z1 = sp.sweep_draws(self.prob.shape, self.seed, self.sweeps_done, self.chain_ids)
             self.s, self.P, _, self.last_sig, self.last_X = mixing_sweep(
                 self.prob, self.s, self.P, g, z0, z1, self.seed, self.sweeps_done, self.chain_ids)
             self.sweeps_done += 1
@@ -175,10 +174,11 @@ class AlternatingChains(sp.Chains):
 
     def sweep(self, n: int = 1):
         for _ in range(n):
-            g, z0, z1, z2, z3 = sp.sweep_draws(self.prob.shape, self.seed, self.sweeps_done, self.chain_ids)
+            g, z0, z1 = sp.sweep_draws(self.prob.shape, self.seed, self.sweeps_done, self.chain_ids)
             if self.sweeps_done % 2 == 0:
+                X = sp.chi2_shell_draws(self.prob.bins.n_b, self.seed, self.sweeps_done, self.chain_ids)
                 self.s, self.P, _, self.last_sig, self.last_X = sp.gibbs_sweep(
-                    self.prob, self.s, self.P, g, z0, z1, z2, z3)
+                    self.prob, self.s, self.P, g, z0, z1, X)
             else:
                 self.s, self.P, _, self.last_sig, self.last_X = mixing_sweep(
                     self.prob, self.s, self.P, g, z0, z1, self.seed, self.sweeps_done, self.chain_ids)

@@ -19,8 +19,9 @@ published by Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy as
   * M0 = 0xD2511F53, M1 = 0xCD9E8D57, W0 = 0x9E3779B9, W1 = 0xBB67AE85.
 
 Stream ids (counter word 3):
-  0 = messenger draw (Alg. 1, first loop), 1 = signal-mode draw and the
-  chi-square draws of the covariance sampler (Alg. 1 second loop, Alg. 2).
+  0 = messenger draw (Alg. 1, first loop), 1 = signal-mode draw (Alg. 1
+  second loop), 2 = over-dispersed starts, 4 = the mixing sampler's proposals
+  (Alg. 3), 5 = the chi-square draw of each shell (Alg. 2 on shells).
 """
 from __future__ import annotations
 
@@ -36,6 +37,7 @@ STREAM_MESSENGER = 0
 STREAM_MODES = 1
 STREAM_START = 2   # over-dispersed starting powers (sampler.Chains)
 STREAM_MIXING = 4  # the mixing sampler's per-shell proposals (oracle/mixing.py)
+STREAM_CHI2 = 5    # the chi-square draw of each shell (sampler.chi2_shell_draws)
 
 
 def philox4x32_10(c0, c1, c2, c3, seed: int):

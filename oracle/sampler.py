@@ -17,7 +17,10 @@ Conventions (where the paper leaves them open, these are the readings taken):
   after the t-conditional in Sec. 3.1).
 * Signal covariance S_hat_k = (M / V) P(bin(k)), and S_hat = 0 at k = 0.
 * Random draws: Philox4x32-10 keyed by the seed with counter
-  (index, sweep, chain, stream) (``oracle.philox``).
+  (index, sweep, chain, stream) (``oracle.philox``): the messenger normals
+  (stream 0), the modes' complex noise (stream 1, two modes per call) and one
+  chi-square variate per shell (stream 5); see ``sweep_draws`` and
+  ``chi2_shell_draws``.
 """
 from __future__ import annotations
 
@@ -147,11 +150,9 @@ def signal_draw(t_hat, S_hat, T_hat: float, xi):
 # Sec. 3.2 / Alg. 2 on k-shells: the covariance draw P | s.
 # --------------------------------------------------------------------------
 
-def shell_sums(bins: BinTable, s_hat, z2, z3):
-    """sigma_b = sum_{j in b} w_j |s_hat_j|^2 and X_b = sum of n_b squared
-    unit normals (w_j of them per stored mode: z2^2, plus z3^2 if w_j = 2).
-
-    The DC mode belongs to no bin.  Shapes: (chains, B+1) each.
+def shell_sums(bins: BinTable, s_hat):
+    """sigma_b = sum_{j in b} w_j |s_hat_j|^2 over the stored modes of shell b
+    (w_j its dof weight).  The DC mode belongs to no shell.  Shape (chains, B+1).
     """
     B1 = bins.n_bins + 1
     idx = bins.bin_of.reshape(-1)
@@ -159,13 +160,61 @@ def shell_sums(bins: BinTable, s_hat, z2, z3):
     keep = idx >= 0
     C = s_hat.shape[0]
     sig = np.zeros((C, B1))
-    X = np.zeros((C, B1))
     a2 = (np.abs(s_hat) ** 2).reshape(C, -1)
-    chi = (z2 ** 2).reshape(C, -1) + np.where(w == 2, 1.0, 0.0) * (z3 ** 2).reshape(C, -1)
     for c in range(C):
         sig[c] = np.bincount(idx[keep], weights=(w * a2[c])[keep], minlength=B1)
-        X[c] = np.bincount(idx[keep], weights=chi[c][keep], minlength=B1)
-    return sig, X
+    return sig
+
+
+# Marsaglia & Tsang (2000), "A simple method for generating gamma variables",
+# ACM TOMS 26(3): for shape alpha >= 1 with d = alpha - 1/3, c = 1/sqrt(9 d),
+# x a unit normal and v = (1 + c x)^3, the value d v is accepted when v > 0 and
+# ln U < x^2/2 + d - d v + d ln v (U uniform); accepted values are Gamma(alpha, 1).
+CHI2_MAX_ATTEMPTS = 64
+
+
+def chi2_shell_draws(n_b, seed: int, sweep: int, chain_ids: Sequence[int]):
+    """X_b ~ chi^2_{n_b} for every shell b and chain (the chi-square variate of
+    Alg. 2 on shells, drawn once per shell), shape (chains, B+1).
+
+    Random numbers: Philox stream 5, attempt k of shell b uses the call
+    (b + 256 k, sweep, chain, 5).
+      n_b = 1:  X = z^2, z the first Box-Muller normal of call (b, sweep, chain, 5)
+                (Alg. 2 literally: u = G^2).
+      n_b >= 2: X = 2 Gamma(n_b / 2) by Marsaglia & Tsang with alpha = n_b/2 >= 1:
+                attempt k takes x = the first Box-Muller normal of words (w0, w1)
+                and U = U(w2); the first accepted attempt gives X = 2 d v.
+      n_b = 0, or no acceptance in 64 attempts: nan (the shell keeps its P).
+    """
+    n_b = np.asarray(n_b, dtype=np.int64)
+    B1 = n_b.size
+    C = len(chain_ids)
+    X = np.full((C, B1), np.nan)
+    for ci, cid in enumerate(chain_ids):
+        for b in range(B1):
+            nb = int(n_b[b])
+            if nb == 0:
+                continue
+            if nb == 1:
+                w = ph.philox4x32_10(np.uint64(b), sweep, cid, ph.STREAM_CHI2, seed)
+                z = float(ph.box_muller(w[0], w[1])[0])
+                X[ci, b] = z * z
+                continue
+            alpha = 0.5 * nb
+            d = alpha - 1.0 / 3.0
+            c = 1.0 / np.sqrt(9.0 * d)
+            for k in range(CHI2_MAX_ATTEMPTS):
+                w = ph.philox4x32_10(np.uint64(b + 256 * k), sweep, cid, ph.STREAM_CHI2, seed)
+                x = float(ph.box_muller(w[0], w[1])[0])
+                v = 1.0 + c * x
+                if v <= 0.0:
+                    continue
+                v = v * v * v
+                u = float(ph.uniform_open0(w[2]))
+                if np.log(u) < 0.5 * x * x + d - d * v + d * np.log(v):
+                    X[ci, b] = 2.0 * d * v
+                    break
+    return X
 
 
 def covariance_draw(sig, X, n_b, P_prev, V: float, M: int):
@@ -174,12 +223,13 @@ def covariance_draw(sig, X, n_b, P_prev, V: float, M: int):
     With Jeffreys' prior 1/S_b and the Gaussian likelihood of the n_b real
     degrees of freedom in shell b, S_b | s ~ InvGamma(n_b/2, sigma_b/2), i.e.
     S_b = sigma_b / X_b with X_b ~ chi^2_{n_b}; for n_b = 1 this is exactly
-    Alg. 2 (u = G^2, S = |s|^2/u).  P_b = (V/M) S_b.  Empty shells keep their
-    previous value.
+    Alg. 2 (u = G^2, S = |s|^2/u).  P_b = (V/M) S_b.  Empty shells, and shells
+    whose sigma_b or X_b is not positive and finite, keep their previous value.
     """
     P = np.array(P_prev, dtype=np.float64, copy=True)
-    has = n_b > 0
-    P[..., has] = (V / M) * sig[..., has] / X[..., has]
+    ok = (np.broadcast_to(n_b > 0, P.shape) & np.isfinite(X) & (X > 0)
+          & np.isfinite(sig) & (sig > 0))
+    P[ok] = (V / M) * sig[ok] / X[ok]
     return P
 
 
@@ -188,24 +238,37 @@ def covariance_draw(sig, X, n_b, P_prev, V: float, M: int):
 # --------------------------------------------------------------------------
 
 def sweep_draws(shape, seed: int, sweep: int, chain_ids: Sequence[int]):
-    """All unit normals one sweep consumes, for each chain id.
+    """The unit normals one sweep's messenger and signal draws consume, per chain.
 
     Messenger: voxel i uses call (i // 4, sweep, chain, 0), normal number i % 4.
-    Modes: stored mode j uses call (j, sweep, chain, 1); z0, z1 build xi, z2, z3
-    feed the chi-square of Alg. 2.
+    Modes: the stored modes kx and nx - kx at the same (ky, kz) share one call,
+    that of the stored index j' = (kx'*ny + ky)*(nz//2 + 1) + kz with
+    kx' = min(kx, nx - kx); the member with kx <= nx/2 takes the normals
+    (z0, z1) of words (w0, w1), the other (z2, z3) of words (w2, w3).
+    Returns g (chains, nx, ny, nz) and z0, z1 (chains, nx, ny, nz//2+1): the two
+    normals behind each stored mode's complex noise (``mode_noise``).
     """
     nx, ny, nz = shape
     M = nx * ny * nz
-    Mh = nx * ny * (nz // 2 + 1)
-    cid = np.asarray(list(chain_ids), dtype=np.uint64)[:, None]
+    nh = nz // 2 + 1
+    hx = nx // 2
+    cid = np.asarray(list(chain_ids), dtype=np.uint64)
+    C = cid.size
     calls = np.arange((M + 3) // 4, dtype=np.uint64)[None, :]
-    jidx = np.arange(Mh, dtype=np.uint64)[None, :]
-    C = cid.shape[0]
-    n4 = ph.normals4(calls, sweep, cid, ph.STREAM_MESSENGER, seed)
+    n4 = ph.normals4(calls, sweep, cid[:, None], ph.STREAM_MESSENGER, seed)
     g = np.stack(n4, axis=-1).reshape(C, -1)[:, :M].reshape((C, nx, ny, nz))
-    zz = ph.normals4(jidx, sweep, cid, ph.STREAM_MODES, seed)
-    z = [q.reshape((C, nx, ny, nz // 2 + 1)) for q in zz]
-    return g, z[0], z[1], z[2], z[3]
+    kxp = np.arange(hx + 1, dtype=np.uint64)[:, None, None]
+    jp = (kxp * np.uint64(ny) + np.arange(ny, dtype=np.uint64)[None, :, None]) * np.uint64(nh) \
+        + np.arange(nh, dtype=np.uint64)[None, None, :]
+    zz = ph.normals4(jp[None], sweep, cid[:, None, None, None], ph.STREAM_MODES, seed)
+    z0 = np.empty((C, nx, ny, nh))
+    z1 = np.empty((C, nx, ny, nh))
+    z0[:, :hx + 1] = zz[0]
+    z1[:, :hx + 1] = zz[1]
+    hi = np.arange(hx + 1, nx)
+    z0[:, hi] = zz[2][:, nx - hi]
+    z1[:, hi] = zz[3][:, nx - hi]
+    return g, z0, z1
 
 
 # --------------------------------------------------------------------------
@@ -254,19 +317,20 @@ def make_problem(shape, L, N, R, d, n_bins: int, k_edges=None,
     return Problem(shape, L, N, R, d, bins, tau)
 
 
-def gibbs_sweep(prob: Problem, s, P, g, z0, z1, z2, z3, fix_P: bool = False):
+def gibbs_sweep(prob: Problem, s, P, g, z0, z1, X, fix_P: bool = False):
     """One Gibbs sweep with explicit noise: Alg. 1 then Alg. 2 (Sec. 3.2: the
     sequential iteration of the two samples the joint posterior).
 
-    s: (C, nx, ny, nz), P: (C, B+1).  Returns (s_new, P_new, s_hat, sig, X).
-    The map is affine in (s, noise) for fixed P.
+    s: (C, nx, ny, nz), P: (C, B+1), X: (C, B+1) chi-square variates (unused
+    with fix_P).  Returns (s_new, P_new, s_hat, sig, X).  The map is affine in
+    (s, noise) for fixed P.
     """
     t = messenger_draw(s, prob.d, prob.N, prob.R, prob.tau, g)
     t_hat = ont(t)
     xi = mode_noise(prob.bins, z0, z1)
     s_hat = signal_draw(t_hat, prob.S_hat(P), prob.tau, xi)
     s_new = ont_inv(s_hat, prob.shape)
-    sig, X = shell_sums(prob.bins, s_hat, z2, z3)
+    sig = shell_sums(prob.bins, s_hat)
     if fix_P:
         P_new = np.array(P, dtype=np.float64, copy=True)
     else:
@@ -307,9 +371,9 @@ class Chains:
 
     def sweep(self, n: int = 1):
         for _ in range(n):
-            g, z0, z1, z2, z3 = sweep_draws(self.prob.shape, self.seed,
-                                            self.sweeps_done, self.chain_ids)
+            g, z0, z1 = sweep_draws(self.prob.shape, self.seed, self.sweeps_done, self.chain_ids)
+            X = chi2_shell_draws(self.prob.bins.n_b, self.seed, self.sweeps_done, self.chain_ids)
             self.s, self.P, _, self.last_sig, self.last_X = gibbs_sweep(
-                self.prob, self.s, self.P, g, z0, z1, z2, z3, self.fix_P)
+                self.prob, self.s, self.P, g, z0, z1, X, self.fix_P)
             self.sweeps_done += 1
         return self

@@ -34,8 +34,8 @@ def numpy_loss(prob, logP, d, w, K, seed):
     ch = sampler.Chains(p2, seed=seed, chain_ids=[0], P0=np.exp(logP), fix_P=True)
     s_hat = None
     for k in range(K):
-        g, z0, z1, z2, z3 = sampler.sweep_draws(p2.shape, seed, k, [0])
-        ch.s, _, s_hat, _, _ = sampler.gibbs_sweep(p2, ch.s, ch.P, g, z0, z1, z2, z3, fix_P=True)
+        g, z0, z1 = sampler.sweep_draws(p2.shape, seed, k, [0])
+        ch.s, _, s_hat, _, _ = sampler.gibbs_sweep(p2, ch.s, ch.P, g, z0, z1, None, fix_P=True)
     return float((w * np.abs(s_hat[0]) ** 2).sum()), ch.s[0]
 
 
@@ -109,7 +109,7 @@ def hand_adjoint(prob, logP, d, w, K, seed):
     s = np.zeros(shape)
     keep = []
     for k in range(K):
-        g, z0, z1, _, _ = sampler.sweep_draws(shape, seed, k, [0])
+        g, z0, z1 = sampler.sweep_draws(shape, seed, k, [0])
         t = sampler.messenger_draw(s, d, prob.N, prob.R, T, g[0])
         th = F(t)
         xi = sampler.mode_noise(prob.bins, z0, z1)[0]

@@ -6,8 +6,10 @@
   (s - t) term and N(d; R t, N~) from the likelihood, combined by precisions —
   a different algebraic route to the same law.
 * The mode conditional against the same completing-the-square construction.
-* Alg. 2 on shells: X_b ~ chi^2_{n_b} (KS), the closed-form inverse-gamma
+* Alg. 2 on shells: X_b ~ chi^2_{n_b} drawn once per shell (KS against the
+  chi-square law, moments, independence), the closed-form inverse-gamma
   moments, and the n_b = 1 shell reproducing Alg. 2 literally.
+* The modes' Philox words: each stored mode has a call and word pair of its own.
 * Noiseless, fully observed data return the binned power of the seeded field.
 """
 import itertools
@@ -71,42 +73,50 @@ def test_mode_conditional_by_precisions():
     np.testing.assert_allclose(var, 1.0 / prec, rtol=1e-13)
 
 
-def chi_draws(shape, n_bins, sweeps, seed=5):
-    tab = make_bins(shape, (1.0, 1.0, 1.0), n_bins)
-    prob = sampler.Problem(shape, (1.0, 1.0, 1.0), None, None, None, tab, 1.0)
-    out = []
-    for sw in range(sweeps):
-        _, z0, z1, z2, z3 = sampler.sweep_draws(shape, seed, sw, [0])
-        zero = np.zeros_like(z0, dtype=complex)
-        _, X = sampler.shell_sums(tab, zero, z2, z3)
-        out.append(X[0])
-    return tab, np.array(out)
+def chi_draws(n_b, sweeps, seed=5, chain=0):
+    """X_b for the shells of counts n_b over `sweeps` sweeps, shape (sweeps, B+1)."""
+    return np.array([sampler.chi2_shell_draws(n_b, seed, sw, [chain])[0] for sw in range(sweeps)])
+
+
+NB_LAW = np.array([1, 2, 3, 5, 8, 40, 1000, 200000])
 
 
 def test_shell_chi_square_law():
-    tab, X = chi_draws((8, 8, 8), 4, 300)
+    """X_b ~ chi^2_{n_b}: KS per shell against scipy's chi-square law (small
+    shape parameters, where a wrong d or c of the gamma method shows, and large
+    ones), its mean n_b and variance 2 n_b, and the pooled probability integral
+    transform uniform."""
+    X = chi_draws(NB_LAW, 1500)
     pooled = []
-    for b in range(tab.n_bins + 1):
-        nb = tab.n_b[b]
-        if nb == 0:
-            continue
-        assert st.kstest(X[:, b], "chi2", args=(nb,)).pvalue > 1e-4
-        pooled.append(st.chi2.cdf(X[:, b], nb))
+    for b, nb in enumerate(NB_LAW):
+        x = X[:, b]
+        assert np.all(np.isfinite(x)) and np.all(x > 0)
+        assert st.kstest(x, "chi2", args=(nb,)).pvalue > 1e-4, nb
+        assert abs(x.mean() - nb) < 5 * np.sqrt(2 * nb / x.size), nb
+        assert abs(x.var() / (2 * nb) - 1) < 0.2, nb
+        pooled.append(st.chi2.cdf(x, nb))
     assert st.kstest(np.concatenate(pooled), "uniform").pvalue > 1e-4
+
+
+def test_shell_chi_square_draws_are_independent():
+    """Different shells, chains and sweeps draw from different Philox calls:
+    no correlation between shells or between chains."""
+    nb = np.full(6, 30)
+    X0 = chi_draws(nb, 800, chain=0)
+    X1 = chi_draws(nb, 800, chain=1)
+    for a, b in ((X0[:, 0], X0[:, 1]), (X0[:, 2], X1[:, 2]), (X0[:-1, 3], X0[1:, 3])):
+        assert abs(np.corrcoef(a, b)[0, 1]) < 5 / np.sqrt(a.size)
 
 
 def test_inverse_gamma_moments():
     """P_b = (V/M) sigma_b / X_b: mean sigma/(n_b - 2), variance
     2 sigma^2 / ((n_b - 2)^2 (n_b - 4)) in S_hat units."""
-    tab, X = chi_draws((8, 8, 8), 4, 2000, seed=9)
+    nb_all = np.array([20, 64, 300])
+    X = chi_draws(nb_all, 3000, seed=9)
     V, M = 1.0, 512
-    for b in range(tab.n_bins + 1):
-        nb = tab.n_b[b]
-        if nb < 20:
-            continue
+    for b, nb in enumerate(nb_all):
         sig = 3.7 * nb
-        P = sampler.covariance_draw(np.full((X.shape[0], tab.n_bins + 1), sig), X, tab.n_b,
-                                    np.zeros((X.shape[0], tab.n_bins + 1)), V, M)[:, b]
+        P = sampler.covariance_draw(np.full(X.shape, sig), X, nb_all, np.zeros(X.shape), V, M)[:, b]
         S = P * M / V
         mean = sig / (nb - 2)
         var = 2 * sig ** 2 / ((nb - 2) ** 2 * (nb - 4))
@@ -115,7 +125,9 @@ def test_inverse_gamma_moments():
 
 
 def test_single_mode_shell_is_alg2():
-    """A shell holding one self-conjugate mode (n_b = 1): S = |s_hat|^2 / G^2."""
+    """A shell holding one self-conjugate mode (n_b = 1): S = |s_hat|^2 / G^2
+    with G the first Box-Muller normal of the shell's Philox call."""
+    from oracle import philox as ph
     n, L = 4, 1.0
     kcorner = 2 * np.pi * np.sqrt(12.0)
     edges = np.array([0.0, kcorner - 0.5, kcorner + 0.5])
@@ -123,11 +135,35 @@ def test_single_mode_shell_is_alg2():
     assert tab.n_b[1] == 1 and tab.bin_of[2, 2, 2] == 1
     rng = np.random.default_rng(1)
     s_hat = (rng.standard_normal((1, n, n, 3)) + 0j)
-    _, z0, z1, z2, z3 = sampler.sweep_draws((n, n, n), 3, 0, [0])
-    sig, X = sampler.shell_sums(tab, s_hat, z2, z3)
+    sig = sampler.shell_sums(tab, s_hat)
+    X = sampler.chi2_shell_draws(tab.n_b, 3, 0, [0])
     P = sampler.covariance_draw(sig, X, tab.n_b, np.zeros((1, 3)), L ** 3, n ** 3)
-    u = z2[0, 2, 2, 2] ** 2
+    w = ph.philox4x32_10(1, 0, 0, ph.STREAM_CHI2, 3)
+    u = float(ph.box_muller(w[0], w[1])[0]) ** 2
     assert P[0, 1] * n ** 3 / L ** 3 == pytest.approx(abs(s_hat[0, 2, 2, 2]) ** 2 / u, rel=1e-14)
+
+
+def test_mode_normals_use_each_philox_word_pair_once():
+    """The stored modes kx and n - kx share one Philox call (that of the stored
+    index of min(kx, n - kx)), the first taking words (w0, w1), the second
+    (w2, w3): every stored mode of a sweep has a call and half of its own, and
+    its normals are those of that call."""
+    from oracle import philox as ph
+    for shape in ((8, 8, 8), (6, 4, 8), (5, 4, 6)):
+        nx, ny, nz = shape
+        nh = nz // 2 + 1
+        _, z0, z1 = sampler.sweep_draws(shape, 11, 2, [3])
+        used = set()
+        for kx in range(nx):
+            kxp = min(kx, nx - kx)
+            half = 0 if kx <= nx // 2 else 1
+            for ky in range(ny):
+                for kz in range(nh):
+                    call = (kxp * ny + ky) * nh + kz
+                    assert (call, half) not in used
+                    used.add((call, half))
+                    zz = ph.normals4(call, 2, 3, ph.STREAM_MODES, 11)
+                    assert z0[0, kx, ky, kz] == zz[2 * half] and z1[0, kx, ky, kz] == zz[2 * half + 1]
 
 
 def test_empty_shell_is_held():

@@ -43,7 +43,7 @@ def test_x_draw_is_the_plain_draw_over_sqrt_S():
     prob = sp.make_problem(shape, 6.0, np.full(shape, 0.3), np.ones(shape),
                            rng.normal(size=shape), 3)
     P = np.array([[0.7, 1.3, 0.4, 2.0]]) * prob.V / prob.M
-    g, z0, z1, _, _ = sp.sweep_draws(shape, 5, 0, [0])
+    g, z0, z1 = sp.sweep_draws(shape, 5, 0, [0])
     t_hat = sp.ont(sp.messenger_draw(np.zeros((1,) + shape), prob.d, prob.N, prob.R, prob.tau, g))
     xi = sp.mode_noise(prob.bins, z0, z1)
     S = prob.S_hat(P)

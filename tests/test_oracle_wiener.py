@@ -70,7 +70,7 @@ def affine_sweep_map(prob, P):
     zm = np.zeros((1, shape[0], shape[1], nh))
 
     def run(s, g, z0, z1):
-        out = sampler.gibbs_sweep(prob, s, P, g, z0, z1, zm, zm, fix_P=True)[0]
+        out = sampler.gibbs_sweep(prob, s, P, g, z0, z1, None, fix_P=True)[0]
         return out.reshape(-1)
 
     h = run(zv, zv, zm, zm)
