@@ -1057,14 +1057,14 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
                     const uint64_t* seeds, const mg_options* opt) {
   using V2 = typename VT<T>::c2;
   cudaError_t e;
-  c->d_sweep = dalloc(sizeof(uint32_t), &e);
+  c->d_sweep = dalloc(2 * sizeof(uint32_t), &e);  // [0] sweep counter, [1] the shell draw's finish ticket
   MG_CUDA(c, e);
   c->d_status = dalloc(sizeof(int), &e);
   MG_CUDA(c, e);
   c->d_rec_now = dalloc(sizeof(int), &e);
   MG_CUDA(c, e);
   MG_CUDA(c, cudaMemsetAsync(c->d_rec_now->p, 0, sizeof(int), c->stream));
-  MG_CUDA(c, cudaMemsetAsync(c->d_sweep->p, 0, sizeof(uint32_t), c->stream));
+  MG_CUDA(c, cudaMemsetAsync(c->d_sweep->p, 0, 2 * sizeof(uint32_t), c->stream));
   MG_CUDA(c, cudaMemsetAsync(c->d_status->p, 0, sizeof(int), c->stream));
   size_t max_M = 0;
   std::map<int, int> class_of_n;

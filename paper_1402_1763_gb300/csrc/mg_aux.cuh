@@ -173,68 +173,76 @@ __global__ void widen_kernel(const T* __restrict__ x, const T* __restrict__ g, s
 }
 
 // Shell draw and the next sweep's per-shell coefficients.  One CTA per
-// (chain, shell): sum the per-tile partials in a fixed order (deterministic),
-// then S_b = sigma_b / X_b with X_b ~ chi^2_{n_b}, i.e. S_b | s ~
-// InvGamma(n_b/2, sigma_b/2) from Jeffreys' prior (Sec. 3.2); P_b = (V/M) S_b.
-// Empty shells, and shells whose sums are not positive and finite (flagged),
-// keep their P.  Then a_b = S/(S + tau), sd_b = sqrt(S tau / (S + tau))
-// (Sec. 3.1), stored as (a_b / M, sd_b / sqrt(M)) for pass X; the DC entry is 0.
+// (chain, shell): sum the per-tile partials sigma_b in a fixed order in FP64
+// (deterministic), then S_b = sigma_b / X_b with X_b ~ chi^2_{n_b} drawn once
+// per shell (chi2_shell), i.e. S_b | s ~ InvGamma(n_b/2, sigma_b/2) from
+// Jeffreys' prior (Sec. 3.2, Alg. 2 on shells); P_b = (V/M) S_b.  Empty shells,
+// and shells whose sigma_b or X_b is not positive and finite (flagged), keep
+// their P.  Then a_b = S/(S + tau), sd_b = sqrt(S tau / (S + tau)) (Sec. 3.1),
+// stored as (a_b / M, sd_b / sqrt(M)) for pass X; the DC entry is 0.
 // draw = 0: only recompute the coefficients from P (set-up, mg_set_pk).
 // fix_P != 0: sum the shells but keep P (the signal sampler alone).
+// sweep_ctr (a sweep, not set-up): word 0 is the sweep counter, which the
+// chi-square draws read; the last CTA to finish advances it (word 1 counts
+// the finished CTAs), so no CTA can read an advanced counter.
 template <typename T>
 __global__ void shell_draw_kernel(const DrawDev* __restrict__ chains, int draw, int fix_P, int* status,
                                   uint32_t* sweep_ctr) {
   const DrawDev cd = chains[blockIdx.x];
   const int b = blockIdx.y;
-  if (b > cd.B) return;
+  const bool active = b <= cd.B;  // the same for the whole CTA
   const int B1 = cd.B + 1;
-  __shared__ double r1[256], r2[256];
-  double s1 = 0.0, s2 = 0.0;
-  if (draw) {
-    for (int t = threadIdx.x; t < cd.n_tiles; t += blockDim.x) {
-      s1 += cd.partial[(size_t(t) * B1 + b) * 2 + 0];
-      s2 += cd.partial[(size_t(t) * B1 + b) * 2 + 1];
-    }
+  __shared__ double r1[256];
+  double s1 = 0.0;
+  if (draw && active) {
+    for (int t = threadIdx.x; t < cd.n_tiles; t += blockDim.x) s1 += cd.partial[(size_t(t) * B1 + b) * 2 + 0];
   }
   r1[threadIdx.x] = s1;
-  r2[threadIdx.x] = s2;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      r1[threadIdx.x] += r1[threadIdx.x + w];
-      r2[threadIdx.x] += r2[threadIdx.x + w];
-    }
+    if (threadIdx.x < w) r1[threadIdx.x] += r1[threadIdx.x + w];
     __syncthreads();
   }
   if (threadIdx.x != 0) return;
-  double P = cd.P[b];
-  if (draw) {
-    const double sig = r1[0] * cd.M, chi = r2[0];  // pass X sums w |s_hat|^2 / M
-    cd.sig_last[b] = sig;
-    cd.chi_last[b] = chi;
-    if (!fix_P && cd.n_b[b] > 0) {
-      if (sig > 0.0 && chi > 0.0 && isfinite(sig) && isfinite(chi)) {
-        P = (cd.V / cd.M) * sig / chi;
-      } else {
-        atomicOr(status, kStNumeric);
+  if (active) {
+    double P = cd.P[b];
+    if (draw) {
+      const double sig = r1[0] * cd.M;  // pass X sums w |s_hat|^2 / M
+      double chi = 0.0;
+      if (!fix_P && cd.n_b[b] > 0) {
+        chi = chi2_shell(cd.n_b[b], uint32_t(b), *sweep_ctr, cd.cid, cd.k0, cd.k1);
+        if (sig > 0.0 && chi > 0.0 && isfinite(sig) && isfinite(chi)) {
+          P = (cd.V / cd.M) * sig / chi;
+        } else {
+          atomicOr(status, kStNumeric);
+        }
       }
+      cd.sig_last[b] = sig;
+      cd.chi_last[b] = chi;
+      cd.P[b] = P;
     }
-    cd.P[b] = P;
+    const double Sh = (cd.M / cd.V) * P;
+    const double a = Sh / (Sh + cd.tau);
+    const double sd = sqrt(Sh * cd.tau / (Sh + cd.tau));
+    typename VT<T>::c2* coef = static_cast<typename VT<T>::c2*>(cd.coef);
+    typename VT<T>::c2 v;
+    v.x = T(a / cd.M);
+    v.y = T(sd / sqrt(cd.M));
+    coef[b] = v;
+    if (b == 0) {
+      v.x = T(0);
+      v.y = T(0);
+      coef[cd.B + 1] = v;
+    }
   }
-  const double Sh = (cd.M / cd.V) * P;
-  const double a = Sh / (Sh + cd.tau);
-  const double sd = sqrt(Sh * cd.tau / (Sh + cd.tau));
-  typename VT<T>::c2* coef = static_cast<typename VT<T>::c2*>(cd.coef);
-  typename VT<T>::c2 v;
-  v.x = T(a / cd.M);
-  v.y = T(sd / sqrt(cd.M));
-  coef[b] = v;
-  if (b == 0) {
-    v.x = T(0);
-    v.y = T(0);
-    coef[cd.B + 1] = v;
+  if (sweep_ctr) {
+    __threadfence();
+    const unsigned total = gridDim.x * gridDim.y;
+    if (atomicAdd(sweep_ctr + 1, 1u) == total - 1u) {
+      sweep_ctr[1] = 0u;
+      atomicAdd(sweep_ctr, 1u);
+    }
   }
-  if (sweep_ctr && blockIdx.x == 0 && b == 0) atomicAdd(sweep_ctr, 1u);
 }
 
 // A draw from N(mu, sigma^2) restricted to (0, inf) from shell b's Philox

@@ -5,7 +5,8 @@
 //     mu = S/(S + T) t_hat and sigma^2 = S T/(S + T), T = tau for the unitary
 //     transform; S_hat = (M/V) P(shell) and 0 at k = 0.
 //   * shell sums for the covariance draw (Sec. 3.2, Alg. 2 on shells):
-//     sigma_b = sum w |s_hat|^2 and X_b = sum of w squared unit normals.
+//     sigma_b = sum w |s_hat|^2 (the chi-square variate X_b is drawn once per
+//     shell by the shell draw).
 //
 // A CTA owns 32 consecutive pencils (lanes) and all n values of x.  The FFT of
 // length n = P*Q runs as: stage F1 (DFT_Q per p, from global), exchange through
@@ -21,10 +22,13 @@ namespace mg {
 
 // Shell accumulators per warp: FP32 keeps an error-free (hi, lo) FP32 pair per
 // value (TwoSum), FP64 a plain double; both are combined in FP64 per tile.
+// kWords: the words of the two-value form (adjoint and mixing sweeps); the
+// plain sweep sums one value and uses the first half of each shell's words.
 template <typename T>
 struct Acc;
 template <>
 struct Acc<float> {
+  static constexpr int kWordsPerValue = 2;
   static constexpr int kWords = 4;  // hi1, lo1, hi2, lo2
   static __device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
     const float s = hi + x;
@@ -42,25 +46,35 @@ struct Acc<float> {
     a[2] = h2;
     a[3] = l2;
   }
+  static __device__ __forceinline__ void add1(float* a, float x1) {
+    float h1 = a[0], l1 = a[1];
+    two_sum(h1, l1, x1);
+    a[0] = h1;
+    a[1] = l1;
+  }
 };
 template <>
 struct Acc<double> {
+  static constexpr int kWordsPerValue = 1;
   static constexpr int kWords = 2;
   static __device__ __forceinline__ void add(double* a, double x1, double x2) {
     a[0] += x1;
     a[1] += x2;
   }
+  static __device__ __forceinline__ void add1(double* a, double x1) { a[0] += x1; }
 };
 
-// Segmented warp reduction of (v1, v2) over runs of equal shell id, then the
-// head of each run adds the run's sums to this warp's accumulators.  bin < 0
-// marks lanes that contribute nothing.  When the shell ids do not decrease
-// along the warp (always the case for pencils of consecutive kz at one
-// (kx, ky)) the run heads hold distinct shells and update in parallel;
-// otherwise they update one after another in lane order.  Both orders are
-// fixed, so the sums are deterministic.
-template <typename T>
+// Segmented warp reduction of NV values (v1, and v2 if NV == 2) over runs of
+// equal shell id, then the head of each run adds the run's sums to this warp's
+// accumulators (kWordsPerValue * NV words per shell).  bin < 0 marks lanes
+// that contribute nothing.  When the shell ids do not decrease along the warp
+// (always the case for pencils of consecutive kz at one (kx, ky)) the run
+// heads hold distinct shells and update in parallel; otherwise they update
+// one after another in lane order.  Both orders are fixed, so the sums are
+// deterministic.
+template <typename T, int NV = 2>
 __device__ __forceinline__ void shell_accumulate(T v1, T v2, int bin, T* accw, int lane) {
+  constexpr int kW = Acc<T>::kWordsPerValue * NV;
   const unsigned full = 0xffffffffu;
   const int prevb = __shfl_up_sync(full, bin, 1);
   const bool head = (lane == 0) || (prevb != bin);
@@ -71,20 +85,25 @@ __device__ __forceinline__ void shell_accumulate(T v1, T v2, int bin, T* accw, i
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
     const T o1 = __shfl_down_sync(full, v1, off);
-    const T o2 = __shfl_down_sync(full, v2, off);
+    T o2 = T(0);
+    if constexpr (NV == 2) o2 = __shfl_down_sync(full, v2, off);
     if (lane + off <= run_end) {
       v1 += o1;
-      v2 += o2;
+      if constexpr (NV == 2) v2 += o2;
     }
   }
+  auto add = [&]() {
+    if constexpr (NV == 2) Acc<T>::add(accw + bin * kW, v1, v2);
+    else Acc<T>::add1(accw + bin * kW, v1);
+  };
   const bool writer = head && bin >= 0;
   if (monotone) {
-    if (writer) Acc<T>::add(accw + bin * Acc<T>::kWords, v1, v2);
+    if (writer) add();
   } else {
     unsigned hm = __ballot_sync(full, writer);
     while (hm) {
       const int src = __ffs(hm) - 1;
-      if (lane == src) Acc<T>::add(accw + bin * Acc<T>::kWords, v1, v2);
+      if (lane == src) add();
       __syncwarp();
       hm &= hm - 1;
     }
@@ -118,48 +137,93 @@ __device__ __forceinline__ int mode_shell(int kx, int ky, int kz, const ChainDev
   return bin;
 }
 
-// The signal draw of one stored mode (kx, ky, kz) with its shell's
-// coefficients cf.  F is the unnormalised forward DFT of t, i.e.
-// sqrt(M) t_hat; with cf = (a/M, sd/sqrt(M)) the result is s_hat / sqrt(M),
-// the value the unnormalised inverse transforms turn into s.  Reports
-// w |s_hat|^2 / M (the shell draw multiplies the sums by M) and the mode's w
-// squared normals.
-template <typename T, int N, bool kChi = true>
-__device__ __forceinline__ cx<T> sample_mode(cx<T> F, cx<T> cf, int kx, int ky, int kz, uint32_t sweep,
-                                             uint32_t k0, uint32_t k1, uint32_t cid, T& sig, T& chi) {
+// Philox call (stream 1) shared by the stored modes kx' and n - kx' at
+// (ky, kz), kx' <= n/2: the stored index of (kx', ky, kz).  Mode kx' takes the
+// normals of words (w0, w1), mode n - kx' those of words (w2, w3).
+template <int N>
+__device__ __forceinline__ uint32_t pair_call(int kxp, int ky, int kz) {
+  return uint32_t((kxp * N + ky) * (N / 2 + 1) + kz);
+}
+
+// The complex unit noise xi of one stored mode (kx, ky, kz) (Sec. 3.1, the
+// signal draw's G for a complex mode): (z0 + i z1)/sqrt(2) from its own word
+// pair.  On the kz = 0 and n/2 planes both k and -k are stored: the member with
+// the larger stored index takes the conjugate of its partner's draw, and a
+// self-conjugate mode is real, xi = z0.
+template <typename T, int N>
+__device__ __forceinline__ cx<T> mode_xi(int kx, int ky, int kz, uint32_t sweep, uint32_t k0, uint32_t k1,
+                                         uint32_t cid) {
   constexpr int H = N / 2;
-  const uint32_t j = uint32_t((kx * N + ky) * (H + 1) + kz);
-  const bool edge = (kz == 0) || (kz == H);
-  const u32x4 w = philox4x32_10(j, sweep, cid, kStreamModes, k0, k1);
-  T z0, z1;
-  normal_pair<T>(w.x, w.y, z0, z1);
   const T rs2 = T(0.70710678118654752440);
-  cx<T> xi;
-  T wgt;
-  chi = T(0);
-  if (!edge) {
-    xi = {z0 * rs2, z1 * rs2};
-    if constexpr (kChi) chi = radius2<T>(w.z);  // z2^2 + z3^2 of the pair (w.z, w.w)
-    wgt = T(2);
-  } else {
-    if constexpr (kChi) {
-      T z2, z3;
-      normal_pair<T>(w.z, w.w, z2, z3);
-      chi = z2 * z2;
-    }
-    wgt = T(1);
-    const uint32_t jp = uint32_t(((((N - kx) % N) * N) + ((N - ky) % N)) * (H + 1) + kz);
-    if (jp == j) {
-      xi = {z0, T(0)};
-    } else if (j < jp) {
-      xi = {z0 * rs2, z1 * rs2};
-    } else {
-      const u32x4 wp = philox4x32_10(jp, sweep, cid, kStreamModes, k0, k1);
-      T p0, p1;
-      normal_pair<T>(wp.x, wp.y, p0, p1);
-      xi = {p0 * rs2, -(p1 * rs2)};
+  int sx = kx, sy = ky;
+  T sgn = T(1);
+  bool real = false;
+  if (kz == 0 || kz == H) {
+    const int px = (N - kx) % N, py = (N - ky) % N;
+    const int j = kx * N + ky, jp = px * N + py;  // stored indices, up to a common kz term
+    if (jp == j) real = true;                     // self-conjugate (kx <= n/2: words (w0, w1))
+    else if (jp < j) {
+      sx = px;
+      sy = py;
+      sgn = T(-1);
     }
   }
+  const bool lo = sx <= H;
+  const u32x4 w = philox4x32_10(pair_call<N>(lo ? sx : N - sx, sy, kz), sweep, cid, kStreamModes, k0, k1);
+  T z0, z1;
+  normal_pair<T>(lo ? w.x : w.z, lo ? w.y : w.w, z0, z1);
+  if (real) return {z0, T(0)};
+  return {z0 * rs2, sgn * (z1 * rs2)};
+}
+
+// The noise of the two stored modes kx and n - kx at (ky, kz) (the same mode
+// twice if kx is 0 or n/2), as mode_xi gives it, from one Philox call (plus
+// one for the partner row on the kz = 0 and n/2 planes).  There, for
+// 0 < kx' < n/2 the mode kx' has the smaller stored index of its (k, -k)
+// pair and draws its own noise, while n - kx' takes the conjugate of the
+// draw of (kx', n - ky), words (w0, w1) of that row's call.
+template <typename T, int N>
+__device__ __forceinline__ void xi_pair(int kx, int ky, int kz, uint32_t sweep, uint32_t k0, uint32_t k1,
+                                        uint32_t cid, cx<T>& xa, cx<T>& xb) {
+  constexpr int H = N / 2;
+  const T rs2 = T(0.70710678118654752440);
+  const bool a_lo = kx <= H;
+  const int lo = a_lo ? kx : N - kx;
+  const u32x4 w = philox4x32_10(pair_call<N>(lo, ky, kz), sweep, cid, kStreamModes, k0, k1);
+  T z0, z1, z2, z3;
+  normal_pair<T>(w.x, w.y, z0, z1);
+  normal_pair<T>(w.z, w.w, z2, z3);
+  cx<T> xl = {z0 * rs2, z1 * rs2}, xh = {z2 * rs2, z3 * rs2};
+  if (kz == 0 || kz == H) {
+    const int py = (N - ky) % N;
+    if (lo == 0 || lo == H) {  // x self-paired: the partner is (lo, n - ky)
+      if (py == ky) {
+        xl = {z0, T(0)};
+      } else if (py < ky) {
+        const u32x4 v = philox4x32_10(pair_call<N>(lo, py, kz), sweep, cid, kStreamModes, k0, k1);
+        T p0, p1;
+        normal_pair<T>(v.x, v.y, p0, p1);
+        xl = {p0 * rs2, -(p1 * rs2)};
+      }
+      xh = xl;
+    } else {
+      const u32x4 v = philox4x32_10(pair_call<N>(lo, py, kz), sweep, cid, kStreamModes, k0, k1);
+      T p0, p1;
+      normal_pair<T>(v.x, v.y, p0, p1);
+      xh = {p0 * rs2, -(p1 * rs2)};
+    }
+  }
+  xa = a_lo ? xl : xh;
+  xb = a_lo ? xh : xl;
+}
+
+// The signal draw of one stored mode with its noise xi and its shell's
+// coefficients cf = (a/M, sd/sqrt(M)): F is the unnormalised forward DFT of
+// t, i.e. sqrt(M) t_hat, and the result is s_hat / sqrt(M), the value the
+// unnormalised inverse transforms turn into s.  Reports w |s_hat|^2 / M (the
+// shell draw multiplies the sums by M), w the mode's dof weight.
+template <typename T>
+__device__ __forceinline__ cx<T> signal_draw(cx<T> F, cx<T> cf, cx<T> xi, T wgt, T& sig) {
   const cx<T> s = {cf.re * F.re + cf.im * xi.re, cf.re * F.im + cf.im * xi.im};
   sig = wgt * (s.re * s.re + s.im * s.im);
   return s;
@@ -170,45 +234,17 @@ __device__ __forceinline__ cx<T> sample_mode(cx<T> F, cx<T> cf, int kx, int ky, 
 template <typename T, int N>
 __device__ __forceinline__ cx<T> draw_mode(cx<T> F, int kx, int ky, int kz, bool valid,
                                            const ChainDev<T>& cd, uint32_t sweep, uint32_t k0, uint32_t k1,
-                                           uint32_t cid, int& bin, T& sig, T& chi) {
+                                           uint32_t cid, int& bin, T& sig) {
+  constexpr int H = N / 2;
   cx<T> cf;
   bin = mode_shell<T, N>(kx, ky, kz, cd, cf);
-  const cx<T> s = sample_mode<T, N>(F, cf, kx, ky, kz, sweep, k0, k1, cid, sig, chi);
+  const cx<T> xi = mode_xi<T, N>(kx, ky, kz, sweep, k0, k1, cid);
+  const cx<T> s = signal_draw<T>(F, cf, xi, (kz == 0 || kz == H) ? T(1) : T(2), sig);
   if (!valid || bin < 0) {
     bin = -1;
     sig = T(0);
-    chi = T(0);
   }
   return s;
-}
-
-// The complex unit noise xi of one stored mode (the same draw draw_mode
-// makes), for the adjoint passes, which regenerate the forward noise.
-template <typename T, int N>
-__device__ __forceinline__ cx<T> mode_xi(int kx, int ky, int kz, uint32_t sweep, uint32_t k0, uint32_t k1,
-                                         uint32_t cid) {
-  constexpr int H = N / 2;
-  const uint32_t j = uint32_t((kx * N + ky) * (H + 1) + kz);
-  const T rs2 = T(0.70710678118654752440);
-  uint32_t src = j;
-  T sgn = T(1);
-  if (kz == 0 || kz == H) {
-    const uint32_t jp = uint32_t(((((N - kx) % N) * N) + ((N - ky) % N)) * (H + 1) + kz);
-    if (jp == j) {
-      const u32x4 w = philox4x32_10(j, sweep, cid, kStreamModes, k0, k1);
-      T z0, z1;
-      normal_pair<T>(w.x, w.y, z0, z1);
-      return {z0, T(0)};
-    }
-    if (jp < j) {
-      src = jp;
-      sgn = T(-1);
-    }
-  }
-  const u32x4 w = philox4x32_10(src, sweep, cid, kStreamModes, k0, k1);
-  T z0, z1;
-  normal_pair<T>(w.x, w.y, z0, z1);
-  return {z0 * rs2, sgn * (z1 * rs2)};
 }
 
 template <typename T, int N, int MODE>
@@ -291,6 +327,7 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
   constexpr int NW = NT / 32;
   constexpr bool kAdj = MODE == kXAdjTop || MODE == kXAdjMid;
   constexpr bool kMixDraw = MODE == kXMixDraw, kMixScale = MODE == kXMixScale;
+  constexpr int kNV = (kAdj || kMixDraw) ? 2 : 1;  // values the shell sums carry
   static_assert(NT % 32 == 0, "whole warps");
   V2* xs = reinterpret_cast<V2*>(smem_raw);  // [N][LW], slot p*Q + v
   V2* xs2 = reinterpret_cast<V2*>(smem_raw + S::kXchgBytes);  // adjoint: second input
@@ -390,8 +427,9 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
   // mode n - kx = Q (P-1-u) + (Q-v) (or, in columns 0 and Q/2, the partner in
   // the same column) are both in the thread, share one shell, and enter the
   // shell sums as one term.
-  // Mixing draws accumulate (w |y|^2, w Re(conj(y) F)) instead of the
-  // signal power and the chi-square draws, and leave the modes in k space.
+  // Plain sweeps sum the signal power w |s_hat|^2 alone (the chi-square
+  // variate is drawn per shell by the shell draw); mixing draws accumulate
+  // (w |y|^2, w Re(conj(y) F)) and leave the modes in k space.
   constexpr bool kPair = !kAdj && !kMixScale && Q % 2 == 0 && (LW * (Q / 2)) % NT == 0;
   if constexpr (kMixScale) {
     // s_hat_new / sqrt(M) = y sqrt(S_new / S_old) per shell, then I1.
@@ -468,15 +506,17 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
         V2* sb = xs + (ub * Q + cb) * LW + lane;
         cx<T> cf;
         int bin = mode_shell<T, N>(Q * ua + ca, ky, kz, cd, cf);
-        // Both draws are made unconditionally (a lone mode draws itself twice
-        // and keeps one) so that the two independent Philox and Box-Muller
-        // chains interleave.
-        T sg, ch, sg2, ch2;
+        // The two modes kx and n - kx draw from one Philox call; both draws
+        // are made unconditionally (a lone mode draws itself twice and keeps
+        // one).
         const cx<T> Fa = ldc<T>(sa), Fb = ldc<T>(sb);
-        const cx<T> ya = sample_mode<T, N, !kMixDraw>(Fa, cf, Q * ua + ca, ky, kz, sweep, k0, k1, cid, sg, ch);
-        const cx<T> yb = sample_mode<T, N, !kMixDraw>(Fb, cf, Q * ub + cb, ky, kz, sweep, k0, k1, cid, sg2, ch2);
+        cx<T> xa, xb;
+        xi_pair<T, N>(Q * ua + ca, ky, kz, sweep, k0, k1, cid, xa, xb);
+        const T wgt = (kz == 0 || kz == H) ? T(1) : T(2);
+        T sg, sg2, ch = T(0), ch2 = T(0);
+        const cx<T> ya = signal_draw<T>(Fa, cf, xa, wgt, sg);
+        const cx<T> yb = signal_draw<T>(Fb, cf, xb, wgt, sg2);
         if constexpr (kMixDraw) {
-          const T wgt = (kz == 0 || kz == H) ? T(1) : T(2);
           ch = wgt * (ya.re * Fa.re + ya.im * Fa.im);
           ch2 = wgt * (yb.re * Fb.re + yb.im * Fb.im);
         }
@@ -491,7 +531,8 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
           sg = T(0);
           ch = T(0);
         }
-        shell_accumulate<T>(sg, ch, bin, accw, lane);
+        if constexpr (kMixDraw) shell_accumulate<T, 2>(sg, ch, bin, accw, lane);
+        else shell_accumulate<T, 1>(sg, T(0), bin, accw, lane);
       }
       if constexpr (!kMixDraw) {
         i1_col(va);
@@ -518,27 +559,28 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
       for (int u = 0; u < P; ++u) {
         V2* slot = xs + (u * Q + vq) * LW + lane;
         int bin;
-        T sg, ch;
+        T sg, ch = T(0);
         cx<T> y;
         if constexpr (kMixDraw) {
           const cx<T> F = ldc<T>(slot);
           cx<T> cf;
           bin = mode_shell<T, N>(Q * u + vq, ky, kz, cd, cf);
-          y = sample_mode<T, N, false>(F, cf, Q * u + vq, ky, kz, sweep, k0, k1, cid, sg, ch);
-          ch = ((kz == 0 || kz == H) ? T(1) : T(2)) * (y.re * F.re + y.im * F.im);
+          const T wgt = (kz == 0 || kz == H) ? T(1) : T(2);
+          y = signal_draw<T>(F, cf, mode_xi<T, N>(Q * u + vq, ky, kz, sweep, k0, k1, cid), wgt, sg);
+          ch = wgt * (y.re * F.re + y.im * F.im);
           if (!valid || bin < 0) {
             bin = -1;
             sg = T(0);
             ch = T(0);
           }
         } else if constexpr (!kAdj) {
-          y = draw_mode<T, N>(ldc<T>(slot), Q * u + vq, ky, kz, valid, cd, sweep, k0, k1, cid, bin, sg, ch);
+          y = draw_mode<T, N>(ldc<T>(slot), Q * u + vq, ky, kz, valid, cd, sweep, k0, k1, cid, bin, sg);
         } else {
           y = adjoint_mode<T, N, MODE>(ldc<T>(slot), ldc<T>(xs2 + (u * Q + vq) * LW + lane), Q * u + vq, ky, kz,
                                        valid, cd, sweep, k0, k1, cid, bin, sg, ch);
         }
         stc<T>(slot, y);
-        shell_accumulate<T>(sg, ch, bin, accw, lane);
+        shell_accumulate<T, kNV>(sg, ch, bin, accw, lane);
       }
       if constexpr (!kMixDraw) {
 #pragma unroll
@@ -573,26 +615,30 @@ __device__ __forceinline__ void pass_x_tile(const LaunchArgs<T>& a, int block, u
     }
   }
 
-  // Per-tile shell sums: combine the warps in a fixed order, then FP64.
+  // Per-tile shell sums: combine the warps in a fixed order, then FP64 (the
+  // second value is 0 in plain sweeps).
   double* part = cd.partial + size_t(tile) * B1 * 2;
+  constexpr int kW = Acc<T>::kWordsPerValue * kNV;  // words per shell in a warp's sums
   for (int b = threadIdx.x; b < (kMixScale ? 0 : B1); b += NT) {
     if constexpr (sizeof(T) == 4) {
       float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
       for (int w2 = 0; w2 < NW; ++w2) {
-        const float* ac = acc + (w2 * B1 + b) * 4;
+        const float* ac = acc + w2 * B1 * Acc<T>::kWords + b * kW;
         Acc<float>::two_sum(h1, l1, ac[0]);
         l1 += ac[1];
-        Acc<float>::two_sum(h2, l2, ac[2]);
-        l2 += ac[3];
+        if constexpr (kNV == 2) {
+          Acc<float>::two_sum(h2, l2, ac[2]);
+          l2 += ac[3];
+        }
       }
       part[2 * b + 0] = double(h1) + double(l1);
       part[2 * b + 1] = double(h2) + double(l2);
     } else {
       double s1 = 0.0, s2 = 0.0;
       for (int w2 = 0; w2 < NW; ++w2) {
-        const double* ac = acc + (w2 * B1 + b) * 2;
+        const double* ac = acc + w2 * B1 * Acc<T>::kWords + b * kW;
         s1 += ac[0];
-        s2 += ac[1];
+        if constexpr (kNV == 2) s2 += ac[1];
       }
       part[2 * b + 0] = s1;
       part[2 * b + 1] = s2;

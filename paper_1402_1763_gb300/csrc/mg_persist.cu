@@ -63,35 +63,31 @@ __device__ __forceinline__ void mark_done(unsigned* p) {
 // Shell draw of one chain by one CTA: per shell, the tiles' partials are split
 // over thread groups in a fixed way and combined in a fixed order.
 template <typename T>
-__device__ void draw_chain(const DrawDev& cd, int fix_P, int* status, double* red) {
+__device__ void draw_chain(const DrawDev& cd, int fix_P, int* status, double* red, uint32_t sweep) {
   const int B1 = cd.B + 1;
   const int groups = kPersistThreads / B1;  // >= 1 since B1 <= 255 < 256
   const int b = threadIdx.x % B1, g = threadIdx.x / B1;
-  double s1 = 0.0, s2 = 0.0;
+  double s1 = 0.0;
   if (g < groups) {
-    for (int t = g; t < cd.n_tiles; t += groups) {
+    for (int t = g; t < cd.n_tiles; t += groups)
       s1 += __ldcg(cd.partial + (size_t(t) * B1 + b) * 2 + 0);  // written by other SMs this launch
-      s2 += __ldcg(cd.partial + (size_t(t) * B1 + b) * 2 + 1);
-    }
-    red[(g * B1 + b) * 2 + 0] = s1;
-    red[(g * B1 + b) * 2 + 1] = s2;
+    red[g * B1 + b] = s1;
   }
   __syncthreads();
   if (threadIdx.x < B1) {
-    double sig = 0.0, chi = 0.0;
-    for (int k = 0; k < groups; ++k) {
-      sig += red[(k * B1 + threadIdx.x) * 2 + 0];
-      chi += red[(k * B1 + threadIdx.x) * 2 + 1];
-    }
+    double sig = 0.0;
+    for (int k = 0; k < groups; ++k) sig += red[k * B1 + threadIdx.x];
     sig *= cd.M;  // pass X sums w |s_hat|^2 / M
     const int bb = threadIdx.x;
     double P = cd.P[bb];
-    cd.sig_last[bb] = sig;
-    cd.chi_last[bb] = chi;
+    double chi = 0.0;
     if (!fix_P && cd.n_b[bb] > 0) {
+      chi = chi2_shell(cd.n_b[bb], uint32_t(bb), sweep, cd.cid, cd.k0, cd.k1);  // Alg. 2 on shells
       if (sig > 0.0 && chi > 0.0 && isfinite(sig) && isfinite(chi)) P = (cd.V / cd.M) * sig / chi;
       else atomicOr(status, kStNumeric);
     }
+    cd.sig_last[bb] = sig;
+    cd.chi_last[bb] = chi;
     cd.P[bb] = P;
     const double Sh = (cd.M / cd.V) * P;
     const double a = Sh / (Sh + cd.tau);
@@ -198,7 +194,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) persistent_sweep_kernel(co
       const int gc = u - a.draw_begin;
       const DrawDev cd = a.draw[gc];
       if (wait_for(x_done + gc, unsigned(cd.n_tiles), a.timeout, a.status, &s_flag))
-        draw_chain<T>(cd, a.fix_P, a.status, s_red);
+        draw_chain<T>(cd, a.fix_P, a.status, s_red, __ldcg(a.sweep_ctr));  // advanced only after every draw
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) {

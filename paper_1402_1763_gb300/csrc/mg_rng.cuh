@@ -161,5 +161,44 @@ constexpr uint32_t kStreamMessenger = 0;
 constexpr uint32_t kStreamModes = 1;
 constexpr uint32_t kStreamStart = 2;   // over-dispersed starting powers
 constexpr uint32_t kStreamMixing = 4;  // the mixing sweeps' per-shell proposals
+constexpr uint32_t kStreamChi2 = 5;    // the chi-square variate of each shell
+
+// X ~ chi^2_n for the covariance draw of shell b (Alg. 2 on k-shells, drawn
+// once per shell), in FP64 in both precision forms.
+//   n = 1:  X = z^2, z the first Box-Muller normal of call (b, sweep, chain, 5):
+//           Alg. 2's u = G^2 literally.
+//   n >= 2: X = 2 Gamma(n/2) by Marsaglia & Tsang (2000, ACM TOMS 26(3)):
+//           d = n/2 - 1/3, c = 1/sqrt(9 d); attempt k uses call
+//           (b + 256 k, sweep, chain, 5): x = the first normal of words (w0, w1),
+//           U = U(w2), v = (1 + c x)^3, accepted when v > 0 and
+//           ln U < x^2/2 + d - d v + d ln v, giving X = 2 d v.
+// Every product and sum is rounded on its own (no contraction), in the
+// order written.  Returns -1 if none of 64 attempts is accepted (probability
+// far below 1e-60); the caller then keeps the shell's P.
+__device__ inline double chi2_shell(long long n, uint32_t b, uint32_t sweep, uint32_t cid, uint32_t k0,
+                                    uint32_t k1) {
+  if (n == 1) {
+    const u32x4 w = philox4x32_10(b, sweep, cid, kStreamChi2, k0, k1);
+    double z0, z1;
+    box_muller(w.x, w.y, z0, z1);
+    return __dmul_rn(z0, z0);
+  }
+  const double alpha = 0.5 * double(n);  // exact
+  const double d = __dsub_rn(alpha, 1.0 / 3.0);
+  const double c = __ddiv_rn(1.0, __dsqrt_rn(__dmul_rn(9.0, d)));
+  for (uint32_t k = 0; k < 64; ++k) {
+    const u32x4 w = philox4x32_10(b + 256u * k, sweep, cid, kStreamChi2, k0, k1);
+    double x, x1;
+    box_muller(w.x, w.y, x, x1);
+    double v = __dadd_rn(1.0, __dmul_rn(c, x));
+    if (!(v > 0.0)) continue;
+    v = __dmul_rn(__dmul_rn(v, v), v);
+    const double lhs = ln_u33(w.z);
+    const double rhs = __dadd_rn(__dsub_rn(__dadd_rn(__dmul_rn(__dmul_rn(0.5, x), x), d), __dmul_rn(d, v)),
+                                 __dmul_rn(d, log(v)));
+    if (lhs < rhs) return __dmul_rn(__dmul_rn(2.0, d), v);
+  }
+  return -1.0;
+}
 
 }  // namespace mg
