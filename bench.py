@@ -375,6 +375,21 @@ def run_other_workload(args):
         ms = ev[0].elapsed_time(ev[1]) / args.steps
         line.update(value=m.n ** 3 / (ms * 1e-3), ms_per_step=ms, dtype="f64",
                     config={"workload": w.name, "removed_fraction": m.removed_fraction})
+    elif args.workload == "fp64-256":
+        # the plain FP64 sampler, one chain of the 256^3 data (the headline
+        # line times it too; standalone for its FP64 counters)
+        w = mockgen.workload(3)
+        m = w.mocks[0]
+        g = Sampler.single(m.n, m.L, m.N, m.R, m.d, m.n_bins, 3, precision=64, stream=stream.cuda_stream)
+        g.sweep(args.warmup)
+        g.sync()
+        ev[0].record(stream)
+        g.sweep(args.steps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / args.steps
+        line.update(value=m.n ** 3 / (ms * 1e-3), ms_per_step=ms, dtype="f64",
+                    config={"workload": w.name.replace("fp32-16chains", "fp64-1chain")})
     elif args.workload == "precision-256":
         # The precision form's accuracy as the 256^3 configuration states it:
         # 16 FP32 chains over 2000 sweeps against the FP64 path (which matches
@@ -489,7 +504,8 @@ def main():
     ap.add_argument("--chains", type=int, default=16, help="chains of the record-256 workload")
     ap.add_argument("--workload", default="256-fp32-16chains",
                     choices=["256-fp32-16chains", "batch-48chains", "adjoint-128", "fp64-128holes",
-                             "fp32-vs-fp64-128", "record-256", "mixing-256", "mixing-acf", "precision-256"])
+                             "fp32-vs-fp64-128", "record-256", "mixing-256", "mixing-acf", "precision-256",
+                             "fp64-256"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = replicas.rank_world()

@@ -41,6 +41,30 @@ __device__ __forceinline__ cx<T> cmul_i(cx<T> a) {
   else return {a.im, -a.re};
 }
 
+// FP32 complex adds and subtracts as one packed two-lane instruction (the
+// FADD2 / FFMA2 forms of sm_100 and later): a value's real and imaginary parts
+// are one register pair, so a butterfly's add costs one instruction instead
+// of two.  Each lane rounds exactly as the scalar operation does.
+__device__ __forceinline__ float2 pk(cx<float> a) { return make_float2(a.re, a.im); }
+__device__ __forceinline__ cx<float> unpk(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ float2 psub2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 ra, rb, rr;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rr, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rr;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ cx<float> cadd(cx<float> a, cx<float> b) { return unpk(__fadd2_rn(pk(a), pk(b))); }
+__device__ __forceinline__ cx<float> csub(cx<float> a, cx<float> b) { return unpk(psub2(pk(a), pk(b))); }
+// d + s * (t.im, t.re): the +-i t terms of the radix-2^k butterflies, one FFMA2
+__device__ __forceinline__ cx<float> cfma_swap(cx<float> t, float2 s, cx<float> d) {
+  return unpk(__ffma2_rn(make_float2(t.im, t.re), s, pk(d)));
+}
+
 // cos and sin of 2*pi*i/48 for i = 0..12 (first quadrant, 25 digits).
 __host__ __device__ constexpr double kCos48q(int i) {
   return i == 0 ? 1.0 : i == 1 ? 0.9914448613738104111445575 : i == 2 ? 0.9659258262890682867497432
@@ -114,6 +138,35 @@ struct Dft<4, DIR, T> {
     v[2] = csub(s02, s13);
     v[1] = cadd(d02, d13);
     v[3] = csub(d02, d13);
+  }
+};
+
+// FP32 radix 3 and 4 on packed pairs: the same arithmetic lane by lane, with
+// the +-i factors folded into one FFMA2 of the swapped difference.
+template <int DIR>
+struct Dft<3, DIR, float> {
+  static __device__ __forceinline__ void run(cx<float>* v) {
+    constexpr float h = 0.8660254037844386467637232f;
+    const cx<float> s = cadd(v[1], v[2]);
+    const cx<float> d = csub(v[1], v[2]);
+    const cx<float> m = unpk(__ffma2_rn(pk(s), make_float2(-0.5f, -0.5f), pk(v[0])));
+    v[0] = cadd(v[0], s);
+    // r = DIR i h d = DIR h (-d.im, d.re); v1 = m + r, v2 = m - r
+    v[1] = cfma_swap(d, make_float2(-DIR * h, DIR * h), m);
+    v[2] = cfma_swap(d, make_float2(DIR * h, -DIR * h), m);
+  }
+};
+
+template <int DIR>
+struct Dft<4, DIR, float> {
+  static __device__ __forceinline__ void run(cx<float>* v) {
+    const cx<float> s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const cx<float> s13 = cadd(v[1], v[3]), t = csub(v[1], v[3]);
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    // d13 = DIR i t = DIR (-t.im, t.re); v1 = d02 + d13, v3 = d02 - d13
+    v[1] = cfma_swap(t, make_float2(-float(DIR), float(DIR)), d02);
+    v[3] = cfma_swap(t, make_float2(float(DIR), -float(DIR)), d02);
   }
 };
 

@@ -218,3 +218,33 @@ def test_single_observed_voxel_and_zero_sweeps():
     res = compare_run(mm, 2, 4, 64, [0, 1, 4])
     for cp, es, ep in res:
         assert es <= 1e-12 and ep <= 1e-12, (cp, es, ep)
+
+
+def test_workload_128cubed_holes_fp64_over_1000_sweeps():
+    """The 128^3 FP64 workload with holes draw for draw over its full 1000
+    sweeps, against the oracle's chain stored by
+    tests/golden/make_workload2_golden.py (the oracle takes ~0.5 s per sweep at
+    this size): P(k) and s at 2048 sampled voxels after sweeps 300 and 1000,
+    relative L2 within the FP64 bar 1e-12."""
+    import json
+    import os
+    need_gpu()
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "workload2_128holes_fp64_1000sweeps.json")
+    with open(path) as f:
+        ref = json.load(f)
+    w = mockgen.workload(2)
+    m = w.mocks[0]
+    assert ref["workload"] == w.name and ref["seed"] == w.seeds[0]
+    vox = np.asarray(ref["sample_voxels"])
+    with gpu_sampler(m, m.n_bins, w.seeds[0], 64) as g:
+        done = 0
+        for cp in sorted(int(k) for k in ref["checkpoints"]):
+            g.sweep(cp - done)
+            done = cp
+            want = ref["checkpoints"][str(cp)]
+            s = g.read_s(0).reshape(-1)
+            es = rel_l2(s[vox], want["s_sample"])
+            ep = rel_l2(g.read_pk(0), want["P"])
+            en = abs(np.linalg.norm(s) / want["s_norm"] - 1.0)
+            assert es <= TOL[64] and ep <= TOL[64] and en <= TOL[64], (cp, es, ep, en)
