@@ -113,7 +113,8 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& z0,
 // The FP32 path's Box-Muller on the special-function unit: U = fma(w, 2^-32,
 // 2^-33); -2 ln U from the hardware base-2 logarithm; the angle 2 pi U is
 // shifted by pi into (-pi, pi] so the hardware sine and cosine stay in their
-// accurate range (|error| <= 2^-21.4 there).  The normals agree with the FP64
+// accurate range (|error| <= 2^-21.4 there); since cos(2 pi U - pi) =
+// -cos(2 pi U) and sin(2 pi U - pi) = -sin(2 pi U), both products are negated.  The normals agree with the FP64
 // construction to a few 1e-6 absolute, except as U_a -> 1, where U's FP32
 // rounding (relative 2^-23) moves -2 ln U by up to ~2^-22 and so the radius
 // by up to ~2^-22 / (2 r) (at most 5e-4, for radii below 1e-3).
@@ -121,11 +122,19 @@ __device__ __forceinline__ float u01_fast(uint32_t w) { return fmaf(__uint2float
 
 __device__ __forceinline__ float minus2log_fast(uint32_t w) { return -1.3862943611198906f * __log2f(u01_fast(w)); }
 
+// The radius from the special-function unit's square root (relative error
+// below 2^-22; exact 0 at U = 1), and the shifted angle 2 pi U - pi =
+// 2 pi (w + 1/2) 2^-32 - pi formed from the word in one fused multiply-add.
+__device__ __forceinline__ float sqrt_fast(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float& z0, float& z1) {
-  const float r2 = minus2log_fast(wa);
-  const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+  const float r = sqrt_fast(minus2log_fast(wa));  // -2 ln U >= 0
   float s, c;
-  __sincosf(6.28318530717958647692f * (u01_fast(wb) - 0.5f), &s, &c);
+  constexpr float kTwoPi = 6.28318530717958647692f;
+  __sincosf(fmaf(__uint2float_rn(wb), kTwoPi * 0x1p-32f, kTwoPi * 0x1p-33f - 3.14159265358979323846f), &s, &c);
   z0 = -(r * c);
   z1 = -(r * s);
 }
