@@ -41,10 +41,10 @@ __device__ __forceinline__ void stc(typename VT<T>::c2* p, cx<T> a) {
 }
 
 // sqrt(x) for x >= 0 as the messenger draw needs it: correctly rounded in
-// FP64; in FP32 x * rsqrtf(x) (a few ulp, well inside the FP32 path's error
-// budget, and several instructions cheaper than the correctly rounded root).
+// FP64; in FP32 the special-function unit's root (relative error below 2^-22,
+// well inside the FP32 path's error budget, one instruction).
 __device__ __forceinline__ double msg_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float msg_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ float msg_sqrt(float x) { return sqrt_fast(x); }
 
 // Double-float sums (hi, lo) of FP32 values for the recorded samples: the
 // exact sum of (hi, lo) and q is hi + lo + q; TwoSum (Knuth) gives s + e =
