@@ -604,6 +604,22 @@ def main():
     e2e_s = replicas.max_over_ranks(e2e_s, dd)
     smp.close()
 
+    # end to end including set-up: the context made from the host arrays (N, R,
+    # d in FP64 uploaded, constants and shell table built), 200 sweeps, every
+    # chain's P(k) read back after each
+    e2e_init_sweeps = 200
+    replicas.barrier(dd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    smp2 = Sampler.single(N_GRID, m.L, m.N, m.R, m.d, N_BINS, SEED, precision=32, n_chains=N_CHAINS,
+                          chain_id0=replicas.chain_id_base(rank, N_CHAINS), stream=stream.cuda_stream)
+    for _ in range(e2e_init_sweeps):
+        smp2.sweep(1)
+        mg_read_pk_all(smp2.ctx, pk)
+    e2e_init_s = time.perf_counter() - t0
+    e2e_init_s = replicas.max_over_ranks(e2e_init_s, dd)
+    smp2.close()
+
     # the plain FP64 single-chain sampler on the same data, same GPU
     fp64 = None
     if rank == 0:
@@ -630,15 +646,19 @@ def main():
         peak64 = mg_fp64_fma_peak(stream.cuda_stream)
         fp64["fp64_peak_gflops"] = peak64
         fp64["fp64_peak_kind"] = "measured (DFMA microkernel, mg_fp64_fma_peak)"
-        flops64 = None
+        flops64 = inst64 = None
         fp = os.path.join(ROOT, "profiles", "fp64_flops_256cubed_1chain.json")
         if os.path.exists(fp):
             with open(fp) as f:
                 fj = json.load(f)
             if fj.get("source_hash") == kernel_source_hash():
                 flops64 = fj["fp64_flops_per_sweep"]
+                inst64 = fj["fp64_thread_instructions_per_sweep"]
         fp64["fp64_flops_per_sweep"] = flops64
         fp64["fp64_frac"] = (flops64 / (ms64 * 1e-3) / 1e9 / peak64) if flops64 else None
+        # DADD and DMUL occupy the FP64 pipe like a DFMA: its occupancy is the
+        # FP64 instruction rate against the DFMA rate (peak flops / 2)
+        fp64["fp64_pipe_frac"] = (inst64 / (ms64 * 1e-3) / 1e9 / (peak64 / 2)) if inst64 else None
 
     # comparison only: the library transforms (cuFFT via torch.fft) of one
     # sweep's work, one forward R2C and one inverse C2R 3D FFT per chain, with
@@ -690,6 +710,11 @@ def main():
                            "frac": sweep_bytes / (ms * 1e-3) / 1e9 / peak},
         "e2e": {"value": units_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": N_CHAINS * (N_BINS + 1) * 8},
+        "e2e_with_setup": {"value": units_per_step * e2e_init_sweeps / e2e_init_s, "unit": UNIT,
+                           "sweeps": e2e_init_sweeps, "seconds": e2e_init_s,
+                           "h2d_bytes": 3 * M * 8, "d2h_bytes": e2e_init_sweeps * N_CHAINS * (N_BINS + 1) * 8,
+                           "note": "context made from host arrays (N, R, d in FP64) inside the timed region, "
+                                   "then the sweeps, every chain's P(k) read back after each"},
         "init_seconds": init_s,
         "gpu_launches": args.steps * 3,
         "clocks": clk,
