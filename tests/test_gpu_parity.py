@@ -248,3 +248,34 @@ def test_workload_128cubed_holes_fp64_over_1000_sweeps():
             ep = rel_l2(g.read_pk(0), want["P"])
             en = abs(np.linalg.norm(s) / want["s_norm"] - 1.0)
             assert es <= TOL[64] and ep <= TOL[64] and en <= TOL[64], (cp, es, ep, en)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_shell_chi_square_variates_match_oracle(precision):
+    """The chi-square variate of each shell (Alg. 2 on shells, drawn once per
+    shell in FP64 in both precision forms) against the oracle's draws, sweep by
+    sweep: a shell holding one self-conjugate mode (n_b = 1: u = G^2, Alg. 2
+    literally), a large shell (Marsaglia-Tsang) and an empty overflow shell
+    (held)."""
+    need_gpu()
+    from paper_1402_1763_gb300 import Sampler
+    n, L = 8, 1.0
+    kc = 2 * np.pi * np.sqrt(3 * (n // 2) ** 2)  # |k| of the corner mode (n/2, n/2, n/2)
+    edges = np.array([0.0, kc - 0.1, kc + 0.1])
+    rng = np.random.default_rng(19)
+    R = np.ones((n, n, n))
+    N = np.full((n, n, n), 0.5)
+    d = rng.standard_normal((n, n, n))
+    prob = sampler.make_problem((n, n, n), L, N, R, d, 2, k_edges=edges)
+    assert list(prob.bins.n_b) == [n ** 3 - 2, 1, 0]
+    orc = sampler.Chains(prob, seed=23, chain_ids=[0, 1])
+    with Sampler.single(n, L, N, R, d, 2, 23, precision=precision, n_chains=2, k_edges=edges) as g:
+        for _ in range(6):
+            orc.sweep(1)
+            g.sweep(1)
+            for c in range(2):
+                st = g.read_stats(c)
+                np.testing.assert_array_equal(st["n_b"], prob.bins.n_b)
+                np.testing.assert_allclose(st["chi_b"][:2], orc.last_X[c][:2], rtol=1e-12)
+                assert st["chi_b"][2] == 0.0  # empty shell: nothing drawn, P held
+                assert rel_l2(g.read_pk(c), orc.P[c]) <= TOL[precision]
