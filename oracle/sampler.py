@@ -120,21 +120,31 @@ def mode_noise(bins: BinTable, z0, z1):
     """Complex unit noise xi per stored mode of a real field.
 
     Interior modes (0 < kz < nz/2): xi = (z0 + i z1)/sqrt(2).  On the kz = 0 and
-    kz = nz/2 planes both k and -k are stored; the member with the smaller
-    stored index is canonical and draws (z0 + i z1)/sqrt(2) from its own
-    counter, its partner takes the complex conjugate of that same value.
-    Self-conjugate modes (k = -k) are real: xi = z0.  This keeps s_hat the
-    transform of a real field while every full-grid dof has unit variance.
+    kz = nz/2 planes both k and -k are stored; of each pair the member with
+    the smaller key ky*nx + kx (so the row 0 < ky < ny/2, or, in the rows
+    ky = 0 and ny/2, the smaller kx) is canonical and draws
+    (z0 + i z1)/sqrt(2) from its own normals, its partner takes the complex
+    conjugate of that same value.  Self-conjugate modes (k = -k) are real:
+    xi = z0.  This keeps s_hat the transform of a real field while every
+    full-grid dof has unit variance.  (With the pairing of ``sweep_draws``, a
+    row ky of an edge plane and its partner row ny - ky then take all their
+    noise from the calls of one of the two rows.)
     """
     zc = (z0 + 1j * z1) / np.sqrt(2.0)
     flat_c = zc.reshape(zc.shape[:-3] + (-1,))
     flat_r = z0.reshape(z0.shape[:-3] + (-1,))
     part = bins.partner.reshape(-1)
     own = np.arange(part.size)
+    nx, ny, nz = bins.shape
+    nh = nz // 2 + 1
+
+    def key(j):  # ky * nx + kx of stored index j = (kx * ny + ky) * nh + kz
+        return ((j // nh) % ny) * nx + j // (ny * nh)
+
     xi = flat_c.copy()
     plane = bins.edge_plane.reshape(-1)
     selfc = plane & (part == own)
-    lower = plane & (part < own)
+    lower = plane & (key(part) < key(own))
     xi[..., selfc] = flat_r[..., selfc]
     xi[..., lower] = np.conj(flat_c[..., part[lower]])
     return xi.reshape(zc.shape)

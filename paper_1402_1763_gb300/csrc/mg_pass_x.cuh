@@ -147,41 +147,39 @@ __device__ __forceinline__ uint32_t pair_call(int kxp, int ky, int kz) {
 
 // The complex unit noise xi of one stored mode (kx, ky, kz) (Sec. 3.1, the
 // signal draw's G for a complex mode): (z0 + i z1)/sqrt(2) from its own word
-// pair.  On the kz = 0 and n/2 planes both k and -k are stored: the member with
-// the larger stored index takes the conjugate of its partner's draw, and a
-// self-conjugate mode is real, xi = z0.
+// pair of the call it shares with n - kx.  On the kz = 0 and n/2 planes both
+// k and -k are stored: of each pair the member with the smaller ky n + kx is
+// canonical and draws its own noise, the other takes the conjugate of it,
+// and a self-conjugate mode is real, xi = z0.  Canonical modes lie in rows
+// ky <= n - ky, so a row ky > n/2 takes every draw from the call of row
+// n - ky: mode kx there is the conjugate of mode n - kx of that row, i.e. of
+// the other word pair (the same one when kx is 0 or n/2).
 template <typename T, int N>
 __device__ __forceinline__ cx<T> mode_xi(int kx, int ky, int kz, uint32_t sweep, uint32_t k0, uint32_t k1,
                                          uint32_t cid) {
   constexpr int H = N / 2;
   const T rs2 = T(0.70710678118654752440);
-  int sx = kx, sy = ky;
-  T sgn = T(1);
-  bool real = false;
-  if (kz == 0 || kz == H) {
-    const int px = (N - kx) % N, py = (N - ky) % N;
-    const int j = kx * N + ky, jp = px * N + py;  // stored indices, up to a common kz term
-    if (jp == j) real = true;                     // self-conjugate (kx <= n/2: words (w0, w1))
-    else if (jp < j) {
-      sx = px;
-      sy = py;
-      sgn = T(-1);
-    }
-  }
-  const bool lo = sx <= H;
-  const u32x4 w = philox4x32_10(pair_call<N>(lo ? sx : N - sx, sy, kz), sweep, cid, kStreamModes, k0, k1);
+  const bool a_lo = kx <= H;
+  const int lo = a_lo ? kx : N - kx;
+  const bool selfx = lo == 0 || lo == H;  // kx = n - kx (mod n)
+  const bool edge = kz == 0 || kz == H;
+  const int py = (N - ky) % N;
+  const bool flip = edge && py < ky;         // conjugate of row py's draw
+  const bool ypair = edge && py == ky;       // kx and n - kx are each other's partners
+  const bool use_hi = flip ? (a_lo && !selfx) : (!ypair && !a_lo);
+  const bool conj = flip || (ypair && !a_lo);
+  const u32x4 w = philox4x32_10(pair_call<N>(lo, flip ? py : ky, kz), sweep, cid, kStreamModes, k0, k1);
   T z0, z1;
-  normal_pair<T>(lo ? w.x : w.z, lo ? w.y : w.w, z0, z1);
-  if (real) return {z0, T(0)};
-  return {z0 * rs2, sgn * (z1 * rs2)};
+  normal_pair<T>(use_hi ? w.z : w.x, use_hi ? w.w : w.y, z0, z1);
+  if (ypair && selfx) return {z0, T(0)};
+  return {z0 * rs2, conj ? -(z1 * rs2) : z1 * rs2};
 }
 
 // The noise of the two stored modes kx and n - kx at (ky, kz) (the same mode
-// twice if kx is 0 or n/2), as mode_xi gives it, from one Philox call (plus
-// one for the partner row on the kz = 0 and n/2 planes).  There, for
-// 0 < kx' < n/2 the mode kx' has the smaller stored index of its (k, -k)
-// pair and draws its own noise, while n - kx' takes the conjugate of the
-// draw of (kx', n - ky), words (w0, w1) of that row's call.
+// twice if kx is 0 or n/2), as mode_xi gives it, from one Philox call: words
+// (w0, w1) for the member with kx <= n/2 and (w2, w3) for the other, of the
+// row's own call, or on the kz = 0 and n/2 planes for rows ky > n/2 the
+// conjugates of the crossed pairs of row n - ky's call.
 template <typename T, int N>
 __device__ __forceinline__ void xi_pair(int kx, int ky, int kz, uint32_t sweep, uint32_t k0, uint32_t k1,
                                         uint32_t cid, cx<T>& xa, cx<T>& xb) {
@@ -189,28 +187,23 @@ __device__ __forceinline__ void xi_pair(int kx, int ky, int kz, uint32_t sweep, 
   const T rs2 = T(0.70710678118654752440);
   const bool a_lo = kx <= H;
   const int lo = a_lo ? kx : N - kx;
-  const u32x4 w = philox4x32_10(pair_call<N>(lo, ky, kz), sweep, cid, kStreamModes, k0, k1);
+  const bool selfx = lo == 0 || lo == H;
+  const bool edge = kz == 0 || kz == H;
+  const int py = (N - ky) % N;
+  const bool flip = edge && py < ky;
+  const u32x4 w = philox4x32_10(pair_call<N>(lo, flip ? py : ky, kz), sweep, cid, kStreamModes, k0, k1);
   T z0, z1, z2, z3;
   normal_pair<T>(w.x, w.y, z0, z1);
   normal_pair<T>(w.z, w.w, z2, z3);
   cx<T> xl = {z0 * rs2, z1 * rs2}, xh = {z2 * rs2, z3 * rs2};
-  if (kz == 0 || kz == H) {
-    const int py = (N - ky) % N;
-    if (lo == 0 || lo == H) {  // x self-paired: the partner is (lo, n - ky)
-      if (py == ky) {
-        xl = {z0, T(0)};
-      } else if (py < ky) {
-        const u32x4 v = philox4x32_10(pair_call<N>(lo, py, kz), sweep, cid, kStreamModes, k0, k1);
-        T p0, p1;
-        normal_pair<T>(v.x, v.y, p0, p1);
-        xl = {p0 * rs2, -(p1 * rs2)};
-      }
-      xh = xl;
-    } else {
-      const u32x4 v = philox4x32_10(pair_call<N>(lo, py, kz), sweep, cid, kStreamModes, k0, k1);
-      T p0, p1;
-      normal_pair<T>(v.x, v.y, p0, p1);
-      xh = {p0 * rs2, -(p1 * rs2)};
+  if (edge) {
+    if (flip) {
+      const cx<T> l = xl;
+      xl = selfx ? cconj(l) : cconj(xh);
+      xh = selfx ? xl : cconj(l);
+    } else if (py == ky) {
+      xl = selfx ? cx<T>{z0, T(0)} : xl;
+      xh = selfx ? xl : cconj(xl);
     }
   }
   xa = a_lo ? xl : xh;

@@ -166,6 +166,41 @@ def test_mode_normals_use_each_philox_word_pair_once():
                     assert z0[0, kx, ky, kz] == zz[2 * half] and z1[0, kx, ky, kz] == zz[2 * half + 1]
 
 
+def test_edge_plane_noise_is_conjugate_symmetric_with_lower_rows_canonical():
+    """The kz = 0 and nz/2 planes store both k and -k.  There xi(-k) must be the
+    conjugate of xi(k) and a self-conjugate mode real (xi = z0), so that s_hat
+    stays the transform of a real field; the canonical member of each pair is
+    the one with the smaller ky*nx + kx and takes its own (z0 + i z1)/sqrt(2).
+    Hence every canonical mode lies in a row ky <= ny - ky: the noise of rows ky
+    and ny - ky comes from the calls of the lower of the two alone.  Checked
+    mode by mode, on even and odd shapes; a rule keyed on the stored index (kx
+    first) fails the row property."""
+    for shape in ((8, 8, 8), (6, 4, 8), (5, 4, 6), (4, 5, 4)):
+        nx, ny, nz = shape
+        nh = nz // 2 + 1
+        tab = make_bins(shape, (1.0, 1.0, 1.0), 1, k_edges=np.array([0.0, 1e3]))
+        _, z0, z1 = sampler.sweep_draws(shape, 11, 2, [3])
+        xi = sampler.mode_noise(tab, z0, z1)[0]
+        n_edge = 0
+        for kx in range(nx):
+            for ky in range(ny):
+                for kz in range(nh):
+                    own = (z0[0, kx, ky, kz] + 1j * z1[0, kx, ky, kz]) / np.sqrt(2.0)
+                    if not tab.edge_plane[kx, ky, kz]:
+                        assert xi[kx, ky, kz] == own
+                        continue
+                    n_edge += 1
+                    px, py = (-kx) % nx, (-ky) % ny
+                    if (px, py) == (kx, ky):
+                        assert xi[kx, ky, kz] == z0[0, kx, ky, kz]
+                        continue
+                    assert xi[px, py, kz] == np.conj(xi[kx, ky, kz])
+                    if ky * nx + kx < py * nx + px:
+                        assert xi[kx, ky, kz] == own
+                        assert ky <= py
+        assert n_edge == 2 * nx * ny
+
+
 def test_empty_shell_is_held():
     tab = make_bins((8, 8, 8), (1.0, 1.0, 1.0), 8)
     # B = 8 linear shells on an 8^3 grid are k_Nyq/8 = k_f/2 wide: |m| = 1 is
