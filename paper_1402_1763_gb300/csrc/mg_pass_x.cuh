@@ -158,7 +158,6 @@ template <typename T, int N>
 __device__ __forceinline__ cx<T> mode_xi(int kx, int ky, int kz, uint32_t sweep, uint32_t k0, uint32_t k1,
                                          uint32_t cid) {
   constexpr int H = N / 2;
-  const T rs2 = T(0.70710678118654752440);
   const bool a_lo = kx <= H;
   const int lo = a_lo ? kx : N - kx;
   const bool selfx = lo == 0 || lo == H;  // kx = n - kx (mod n)
@@ -169,10 +168,10 @@ __device__ __forceinline__ cx<T> mode_xi(int kx, int ky, int kz, uint32_t sweep,
   const bool use_hi = flip ? (a_lo && !selfx) : (!ypair && !a_lo);
   const bool conj = flip || (ypair && !a_lo);
   const u32x4 w = philox4x32_10(pair_call<N>(lo, flip ? py : ky, kz), sweep, cid, kStreamModes, k0, k1);
-  T z0, z1;
-  normal_pair<T>(use_hi ? w.z : w.x, use_hi ? w.w : w.y, z0, z1);
-  if (ypair && selfx) return {z0, T(0)};
-  return {z0 * rs2, conj ? -(z1 * rs2) : z1 * rs2};
+  T z0, z1;  // the normals / sqrt(2)
+  half_normal_pair<T>(use_hi ? w.z : w.x, use_hi ? w.w : w.y, z0, z1);
+  if (ypair && selfx) return {z0 * T(1.41421356237309504880), T(0)};
+  return {z0, conj ? -z1 : z1};
 }
 
 // The noise of the two stored modes kx and n - kx at (ky, kz) (the same mode
@@ -184,7 +183,6 @@ template <typename T, int N>
 __device__ __forceinline__ void xi_pair(int kx, int ky, int kz, uint32_t sweep, uint32_t k0, uint32_t k1,
                                         uint32_t cid, cx<T>& xa, cx<T>& xb) {
   constexpr int H = N / 2;
-  const T rs2 = T(0.70710678118654752440);
   const bool a_lo = kx <= H;
   const int lo = a_lo ? kx : N - kx;
   const bool selfx = lo == 0 || lo == H;
@@ -192,17 +190,17 @@ __device__ __forceinline__ void xi_pair(int kx, int ky, int kz, uint32_t sweep, 
   const int py = (N - ky) % N;
   const bool flip = edge && py < ky;
   const u32x4 w = philox4x32_10(pair_call<N>(lo, flip ? py : ky, kz), sweep, cid, kStreamModes, k0, k1);
-  T z0, z1, z2, z3;
-  normal_pair<T>(w.x, w.y, z0, z1);
-  normal_pair<T>(w.z, w.w, z2, z3);
-  cx<T> xl = {z0 * rs2, z1 * rs2}, xh = {z2 * rs2, z3 * rs2};
+  T z0, z1, z2, z3;  // the normals / sqrt(2)
+  half_normal_pair<T>(w.x, w.y, z0, z1);
+  half_normal_pair<T>(w.z, w.w, z2, z3);
+  cx<T> xl = {z0, z1}, xh = {z2, z3};
   if (edge) {
     if (flip) {
       const cx<T> l = xl;
       xl = selfx ? cconj(l) : cconj(xh);
       xh = selfx ? xl : cconj(l);
     } else if (py == ky) {
-      xl = selfx ? cx<T>{z0, T(0)} : xl;
+      xl = selfx ? cx<T>{z0 * T(1.41421356237309504880), T(0)} : xl;
       xh = selfx ? xl : cconj(xl);
     }
   }

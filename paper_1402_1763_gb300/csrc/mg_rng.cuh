@@ -139,6 +139,25 @@ __device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float&
   z1 = -(r * s);
 }
 
+// The same pairs scaled by 1/sqrt(2), the real and imaginary parts of a unit
+// complex normal: the radius is sqrt(-ln U) instead of sqrt(-2 ln U), the
+// angle unchanged (no separate multiplication of each normal).
+__device__ __forceinline__ void box_muller_half(uint32_t wa, uint32_t wb, double& z0, double& z1) {
+  const double r = sqrt(-ln_u33(wa));
+  double s, c;
+  sincos_2pi_u33(wb, s, c);
+  z0 = r * c;
+  z1 = r * s;
+}
+__device__ __forceinline__ void box_muller_fast_half(uint32_t wa, uint32_t wb, float& z0, float& z1) {
+  const float r = sqrt_fast(-0.69314718055994531f * __log2f(u01_fast(wa)));  // -ln U >= 0
+  float s, c;
+  constexpr float kTwoPi = 6.28318530717958647692f;
+  __sincosf(fmaf(__uint2float_rn(wb), kTwoPi * 0x1p-32f, kTwoPi * 0x1p-33f - 3.14159265358979323846f), &s, &c);
+  z0 = -(r * c);
+  z1 = -(r * s);
+}
+
 // Precision dispatch: FP64 uses the table-driven construction above, the
 // FP32 path the special-function-unit one.
 template <typename T>
@@ -150,6 +169,16 @@ __device__ __forceinline__ void normal_pair<double>(uint32_t wa, uint32_t wb, do
 template <>
 __device__ __forceinline__ void normal_pair<float>(uint32_t wa, uint32_t wb, float& z0, float& z1) {
   box_muller_fast(wa, wb, z0, z1);
+}
+template <typename T>
+__device__ __forceinline__ void half_normal_pair(uint32_t wa, uint32_t wb, T& z0, T& z1);
+template <>
+__device__ __forceinline__ void half_normal_pair<double>(uint32_t wa, uint32_t wb, double& z0, double& z1) {
+  box_muller_half(wa, wb, z0, z1);
+}
+template <>
+__device__ __forceinline__ void half_normal_pair<float>(uint32_t wa, uint32_t wb, float& z0, float& z1) {
+  box_muller_fast_half(wa, wb, z0, z1);
 }
 
 // -2 ln U of one word: the squared radius of a Box-Muller pair, i.e. the sum
