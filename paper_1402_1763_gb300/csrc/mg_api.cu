@@ -193,17 +193,18 @@ std::vector<uint8_t> build_bin_table(int n, double L, int B, const double* edges
     }
     tab[m2] = uint8_t(b);
   }
-  // full-grid mode counts per shell
+  // full-grid mode counts per shell: the modes with |m|^2 = m2 counted over
+  // the distinct |m| of each axis, weighted by how many k give that |m|
   n_b->assign(B + 1, 0);
   std::vector<long long> cnt(size_t(max_m2) + 1, 0);
-  std::vector<int> m2_of(n);
-  for (int k = 0; k < n; ++k) {
-    const int m = k <= h ? k : k - n;
-    m2_of[k] = m * m;
-  }
-  for (int a = 0; a < n; ++a)
-    for (int b2 = 0; b2 < n; ++b2)
-      for (int c = 0; c < n; ++c) ++cnt[m2_of[a] + m2_of[b2] + m2_of[c]];
+  std::vector<long long> mult(size_t(h) + 1, 0);
+  for (int k = 0; k < n; ++k) ++mult[std::abs(k <= h ? k : k - n)];
+  for (int a = 0; a <= h; ++a)
+    for (int b2 = 0; b2 <= h; ++b2) {
+      const long long wab = mult[a] * mult[b2];
+      const int s2 = a * a + b2 * b2;
+      for (int c = 0; c <= h; ++c) cnt[s2 + c * c] += wab * mult[c];
+    }
   for (int m2 = 1; m2 <= max_m2; ++m2) (*n_b)[tab[m2]] += cnt[m2];
   return tab;
 }
@@ -1126,23 +1127,24 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
     MG_CUDA(c, cudaGetLastError());
     // compact row store of the messenger constants (observed z-ranges only)
     {
-      const double* Rh = R[gi];
+      // each row's range from R on the device, the offsets (a prefix sum in
+      // row order) on the host
       const int n = g.n;
-      std::vector<uint32_t> ri(size_t(2) * n * n);
+      const size_t rows = size_t(n) * n;
+      auto dlohi = dalloc(rows * sizeof(uint32_t), &e);
+      MG_CUDA(c, e);
+      row_range_kernel<<<1024, 256, 0, c->stream>>>(static_cast<const double*>(dR->p), n, rows,
+                                                    static_cast<uint32_t*>(dlohi->p));
+      MG_CUDA(c, cudaGetLastError());
+      std::vector<uint32_t> lohi(rows);
+      MG_CUDA(c, cudaMemcpyAsync(lohi.data(), dlohi->p, rows * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+      MG_CUDA(c, cudaStreamSynchronize(c->stream));
+      std::vector<uint32_t> ri(2 * rows);
       uint32_t off = 0;
-      for (size_t row = 0; row < size_t(n) * n; ++row) {
-        int lo = n, hi = 0;
-        for (int z = 0; z < n; ++z)
-          if (Rh[row * n + z] > 0) {
-            lo = std::min(lo, z);
-            hi = z + 1;
-          }
-        if (hi <= lo) lo = hi = 0;
-        lo &= ~3;
-        hi = (hi + 3) & ~3;
+      for (size_t row = 0; row < rows; ++row) {
         ri[2 * row] = off;
-        ri[2 * row + 1] = uint32_t(lo) | (uint32_t(hi) << 16);
-        off += uint32_t(hi - lo);
+        ri[2 * row + 1] = lohi[row];
+        off += (lohi[row] >> 16) - (lohi[row] & 0xffffu);
       }
       g.row_info = dalloc(ri.size() * sizeof(uint32_t), &e);
       MG_CUDA(c, e);

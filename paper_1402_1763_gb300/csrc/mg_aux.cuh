@@ -76,6 +76,30 @@ __global__ void messenger_constants_kernel(const double* __restrict__ N, const d
   }
 }
 
+// The observed z-range of each z-row (x, y): [lo, hi) spans the voxels with
+// R > 0, widened to multiples of 4 (lo down, hi up); a row with none gets
+// [0, 0).  One warp per row; lohi[row] = lo | hi << 16.
+__global__ void row_range_kernel(const double* __restrict__ R, int n, size_t rows, uint32_t* __restrict__ lohi) {
+  const int lane = threadIdx.x & 31;
+  const size_t warps = size_t(gridDim.x) * blockDim.x / 32;
+  for (size_t row = (blockIdx.x * size_t(blockDim.x) + threadIdx.x) / 32; row < rows; row += warps) {
+    int lo = n, hi = 0;
+    for (int z = lane; z < n; z += 32)
+      if (R[row * n + z] > 0.0) {
+        lo = min(lo, z);
+        hi = max(hi, z + 1);
+      }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) {
+      if (hi <= lo) lo = hi = 0;
+      lo &= ~3;
+      hi = (hi + 3) & ~3;
+      lohi[row] = uint32_t(lo) | (uint32_t(hi) << 16);
+    }
+  }
+}
+
 // Copy each row's observed z-range of (b, c) into the compact row store.
 template <typename T>
 __global__ void pack_rows_kernel(const typename VT<T>::c2* __restrict__ bc, const uint2* __restrict__ row_info,
