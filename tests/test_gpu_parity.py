@@ -220,6 +220,20 @@ def test_single_observed_voxel_and_zero_sweeps():
         assert es <= 1e-12 and ep <= 1e-12, (cp, es, ep)
 
 
+@pytest.mark.parametrize("n,precision,checkpoints", [(32, 64, [1, 3, 10]), (32, 32, [1, 3, 10]),
+                                                     (256, 32, [1, 2])])
+def test_largest_shell_count(n, precision, checkpoints):
+    """254 shells, the most the shell table holds: at 32^3 most shells are
+    narrower than the spacing of |m| (empty shells held, one-mode shells
+    drawing u = G^2); at 256^3 the per-warp shell sums take 32 KB of pass X's
+    shared memory, two CTAs per SM instead of three."""
+    need_gpu()
+    m = mockgen.make_mock(n, seed=91 + n, n_bins=254)
+    res = compare_run(m, 254, 5, precision, checkpoints)
+    for cp, es, ep in res:
+        assert es <= TOL[precision] and ep <= TOL[precision], (n, cp, es, ep)
+
+
 def test_workload_128cubed_holes_fp64_over_1000_sweeps():
     """The 128^3 FP64 workload with holes draw for draw over its full 1000
     sweeps, against the oracle's chain stored by
