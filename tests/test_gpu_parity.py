@@ -74,7 +74,7 @@ def test_workload_128cubed_holes_fp64_over_100_sweeps():
         assert es <= TOL[64] and ep <= TOL[64], (cp, es, ep)
 
 
-@pytest.mark.parametrize("precision,cluster", [(32, 2), (32, 4), (64, 4)])
+@pytest.mark.parametrize("precision,cluster", [(32, 2), (32, 4), (32, 8), (64, 4)])
 def test_workload_256cubed_sampled_chains(precision, cluster):
     """Full-size 256^3 grid in the benchmark's launch form (16 chains in one
     launch for FP32); the oracle follows chains 0 and 15 for two sweeps."""
@@ -232,6 +232,29 @@ def test_largest_shell_count(n, precision, checkpoints):
     res = compare_run(m, 254, 5, precision, checkpoints)
     for cp, es, ep in res:
         assert es <= TOL[precision] and ep <= TOL[precision], (n, cp, es, ep)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_new_data_mid_chain(precision):
+    """mg_set_data replaces the data d of a running chain (the messenger
+    constants c = gamma d and their packed rows are rebuilt, b and tau stay):
+    3 sweeps on d, then 5 on d' = 0.7 d + 0.2 R, against the oracle whose
+    problem is rebuilt on d' at the same point."""
+    need_gpu()
+    m = mockgen.make_mock(32, seed=57, n_bins=8)
+    d2 = 0.7 * m.d + 0.2 * m.R
+    orc = oracle_chains(m, 8, 6, [0, 1])
+    with gpu_sampler(m, 8, 6, precision, n_chains=2) as g:
+        for sweeps, data_after in ((3, True), (5, False)):
+            orc.sweep(sweeps)
+            g.sweep(sweeps)
+            for c in (0, 1):
+                es = rel_l2(g.read_s(c), orc.s[c])
+                ep = rel_l2(g.read_pk(c), orc.P[c])
+                assert es <= TOL[precision] and ep <= TOL[precision], (sweeps, c, es, ep)
+            if data_after:
+                g.set_data(0, d2)
+                orc.prob = sampler.make_problem(m.shape, m.L, m.N, m.R, d2, 8)
 
 
 def test_workload_128cubed_holes_fp64_over_1000_sweeps():
