@@ -20,7 +20,7 @@ import pytest
 
 import mockgen
 
-from gpu_helpers import TOL, need_gpu, oracle_chains, rel_l2
+from gpu_helpers import TOL, check_elementwise, need_gpu, oracle_chains, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -49,9 +49,11 @@ def test_persistent_mixed_batch_matches_oracle(precision):
             orc = oracle_chains(m, m.n_bins, seeds[gi], [0, 1])
             orc.sweep(3)
             for c in range(2):
-                es = rel_l2(g.read_s(2 * gi + c), orc.s[c])
-                ep = rel_l2(g.read_pk(2 * gi + c), orc.P[c])
+                sg, pg = g.read_s(2 * gi + c), g.read_pk(2 * gi + c)
+                es = rel_l2(sg, orc.s[c])
+                ep = rel_l2(pg, orc.P[c])
                 assert es <= TOL[precision] and ep <= TOL[precision], (gi, c, es, ep)
+                check_elementwise(precision, sg, orc.s[c], pg, orc.P[c], f"persistent batch n={m.n} chain {c}")
 
 
 def test_batching_workload_one_persistent_launch_per_sweep():
@@ -64,9 +66,11 @@ def test_batching_workload_one_persistent_launch_per_sweep():
             m = w.mocks[c]
             orc = oracle_chains(m, m.n_bins, w.seeds[c], [0])
             orc.sweep(2)
-            es = rel_l2(g.read_s(c), orc.s[0])
-            ep = rel_l2(g.read_pk(c), orc.P[0])
+            sg, pg = g.read_s(c), g.read_pk(c)
+            es = rel_l2(sg, orc.s[0])
+            ep = rel_l2(pg, orc.P[0])
             assert es <= TOL[32] and ep <= TOL[32], (c, es, ep)
+            check_elementwise(32, sg, orc.s[0], pg, orc.P[0], f"batching workload chain {c}")
         assert g.sweep_count == 2
 
 

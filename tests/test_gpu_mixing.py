@@ -17,7 +17,7 @@ import pytest
 
 import mockgen
 
-from gpu_helpers import TOL, need_gpu, rel_l2
+from gpu_helpers import TOL, check_elementwise, need_gpu, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -43,8 +43,10 @@ def compare(mock, n_bins, seed, precision, sweeps, follow, n_chains, mixing=1, *
             orc.sweep(1)
             g.sweep(1)
             for k, c in enumerate(follow):
-                es = rel_l2(g.read_s(c), orc.s[k])
-                ep = rel_l2(g.read_pk(c), orc.P[k])
+                sg, pg = g.read_s(c), g.read_pk(c)
+                es = rel_l2(sg, orc.s[k])
+                ep = rel_l2(pg, orc.P[k])
+                check_elementwise(precision, sg, orc.s[k], pg, orc.P[k], f"mixing n={mock.n} sweep {sw} chain {c}")
                 st = g.read_stats(c)
                 if mixing == 1 or sw % 2 == 1:
                     assert np.array_equal(st["chi_b"], orc.last_X[k]), (sw, c, "acceptance flags differ")

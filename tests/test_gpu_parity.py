@@ -14,7 +14,7 @@ import mockgen
 from oracle import philox as ph
 from oracle import sampler
 
-from gpu_helpers import TOL, compare_run, gpu_sampler, need_gpu, oracle_chains, rel_l2
+from gpu_helpers import TOL, check_elementwise, compare_run, gpu_sampler, need_gpu, oracle_chains, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -89,9 +89,11 @@ def test_workload_256cubed_sampled_chains(precision, cluster):
             orc.sweep(1)
             g.sweep(1)
             for k, c in enumerate(follow):
-                es = rel_l2(g.read_s(c), orc.s[k])
-                ep = rel_l2(g.read_pk(c), orc.P[k])
+                sg, pg = g.read_s(c), g.read_pk(c)
+                es = rel_l2(sg, orc.s[k])
+                ep = rel_l2(pg, orc.P[k])
                 assert es <= TOL[precision] and ep <= TOL[precision], (sw, c, es, ep)
+                check_elementwise(precision, sg, orc.s[k], pg, orc.P[k], f"256^3 C={cluster} sweep {sw} chain {c}")
 
 
 def test_batch_of_mixed_sizes_matches_independent_oracles():
@@ -108,9 +110,11 @@ def test_batch_of_mixed_sizes_matches_independent_oracles():
             orc = oracle_chains(m, m.n_bins, seeds[gi], [0, 1])
             orc.sweep(3)
             for c in range(2):
-                es = rel_l2(g.read_s(2 * gi + c), orc.s[c])
-                ep = rel_l2(g.read_pk(2 * gi + c), orc.P[c])
+                sg, pg = g.read_s(2 * gi + c), g.read_pk(2 * gi + c)
+                es = rel_l2(sg, orc.s[c])
+                ep = rel_l2(pg, orc.P[c])
                 assert es <= 1e-12 and ep <= 1e-12, (gi, c, es, ep)
+                check_elementwise(64, sg, orc.s[c], pg, orc.P[c], f"batch n={m.n} chain {c}")
 
 
 def test_fixed_P_and_explicit_edges_and_tau_scale():
@@ -249,9 +253,11 @@ def test_new_data_mid_chain(precision):
             orc.sweep(sweeps)
             g.sweep(sweeps)
             for c in (0, 1):
-                es = rel_l2(g.read_s(c), orc.s[c])
-                ep = rel_l2(g.read_pk(c), orc.P[c])
+                sg, pg = g.read_s(c), g.read_pk(c)
+                es = rel_l2(sg, orc.s[c])
+                ep = rel_l2(pg, orc.P[c])
                 assert es <= TOL[precision] and ep <= TOL[precision], (sweeps, c, es, ep)
+                check_elementwise(precision, sg, orc.s[c], pg, orc.P[c], f"set_data sweep {sweeps} chain {c}")
             if data_after:
                 g.set_data(0, d2)
                 orc.prob = sampler.make_problem(m.shape, m.L, m.N, m.R, d2, 8)
@@ -281,10 +287,13 @@ def test_workload_128cubed_holes_fp64_over_1000_sweeps():
             done = cp
             want = ref["checkpoints"][str(cp)]
             s = g.read_s(0).reshape(-1)
+            pg = g.read_pk(0)
             es = rel_l2(s[vox], want["s_sample"])
-            ep = rel_l2(g.read_pk(0), want["P"])
+            ep = rel_l2(pg, want["P"])
             en = abs(np.linalg.norm(s) / want["s_norm"] - 1.0)
             assert es <= TOL[64] and ep <= TOL[64] and en <= TOL[64], (cp, es, ep, en)
+            check_elementwise(64, s[vox], np.asarray(want["s_sample"]), pg, np.asarray(want["P"]),
+                              f"128^3 holes, 1000-sweep record, sweep {cp}")
 
 
 @pytest.mark.parametrize("precision", [64, 32])
