@@ -610,12 +610,14 @@ def main():
     # host wall time, so it is taken three times and the median reported.
     e2e_init_sweeps = 200
     e2e_init_runs = []
+    e2e_setup_s = []
     for _ in range(3):
         replicas.barrier(dd)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         smp2 = Sampler.single(N_GRID, m.L, m.N, m.R, m.d, N_BINS, SEED, precision=32, n_chains=N_CHAINS,
                               chain_id0=replicas.chain_id_base(rank, N_CHAINS), stream=stream.cuda_stream)
+        e2e_setup_s.append(time.perf_counter() - t0)
         for _ in range(e2e_init_sweeps):
             smp2.sweep(1)
             mg_read_pk_all(smp2.ctx, pk)
@@ -715,7 +717,7 @@ def main():
                 "d2h_bytes_per_step": N_CHAINS * (N_BINS + 1) * 8},
         "e2e_with_setup": {"value": units_per_step * e2e_init_sweeps / e2e_init_s, "unit": UNIT,
                            "sweeps": e2e_init_sweeps, "seconds": e2e_init_s,
-                           "runs_seconds": e2e_init_runs,
+                           "runs_seconds": e2e_init_runs, "setup_seconds": e2e_setup_s,
                            "h2d_bytes": 3 * M * 8, "d2h_bytes": e2e_init_sweeps * N_CHAINS * (N_BINS + 1) * 8,
                            "note": "context made from host arrays (N, R, d in FP64) inside the timed region, "
                                    "then the sweeps, every chain's P(k) read back after each; median of "
