@@ -294,12 +294,12 @@ mg_status upload_descriptors(mg_ctx* c) {
     cudaError_t e;
     sc.d_desc = dalloc(h.size() * sizeof(ChainDev<T>), &e);
     MG_CUDA(c, e);
-    MG_CUDA(c, cudaMemcpy(sc.d_desc->p, h.data(), h.size() * sizeof(ChainDev<T>), cudaMemcpyHostToDevice));
+    MG_CUDA(c, cudaMemcpyAsync(sc.d_desc->p, h.data(), h.size() * sizeof(ChainDev<T>), cudaMemcpyHostToDevice, c->stream));
     sc.h_desc.assign(reinterpret_cast<const char*>(h.data()), reinterpret_cast<const char*>(h.data() + h.size()));
     const auto tw = twiddles<T>(sc.n);
     sc.tw = dalloc(tw.size() * sizeof(V2), &e);
     MG_CUDA(c, e);
-    MG_CUDA(c, cudaMemcpy(sc.tw->p, tw.data(), tw.size() * sizeof(V2), cudaMemcpyHostToDevice));
+    MG_CUDA(c, cudaMemcpyAsync(sc.tw->p, tw.data(), tw.size() * sizeof(V2), cudaMemcpyHostToDevice, c->stream));
     sc.args.clear();
     for (size_t c0 = 0; c0 < sc.chains.size(); c0 += kMaxLaunchChains) {
       LaunchArgs<T> a;
@@ -343,7 +343,7 @@ mg_status upload_descriptors(mg_ctx* c) {
   cudaError_t e;
   c->d_draw = dalloc(dd.size() * sizeof(DrawDev), &e);
   MG_CUDA(c, e);
-  MG_CUDA(c, cudaMemcpy(c->d_draw->p, dd.data(), dd.size() * sizeof(DrawDev), cudaMemcpyHostToDevice));
+  MG_CUDA(c, cudaMemcpyAsync(c->d_draw->p, dd.data(), dd.size() * sizeof(DrawDev), cudaMemcpyHostToDevice, c->stream));
   return MG_OK;
 }
 
@@ -1148,7 +1148,7 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
       }
       g.row_info = dalloc(ri.size() * sizeof(uint32_t), &e);
       MG_CUDA(c, e);
-      MG_CUDA(c, cudaMemcpy(g.row_info->p, ri.data(), ri.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+      MG_CUDA(c, cudaMemcpyAsync(g.row_info->p, ri.data(), ri.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
       g.bc_rows_len = std::max<uint32_t>(off, 4);
       g.bc_rows = dalloc(size_t(g.bc_rows_len) * sizeof(V2), &e);
       MG_CUDA(c, e);
@@ -1161,10 +1161,10 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
     const auto tab = build_bin_table(g.n, g.L, g.B, edges, &g.n_b);
     g.bin_of_m2 = dalloc(tab.size(), &e);
     MG_CUDA(c, e);
-    MG_CUDA(c, cudaMemcpy(g.bin_of_m2->p, tab.data(), tab.size(), cudaMemcpyHostToDevice));
+    MG_CUDA(c, cudaMemcpyAsync(g.bin_of_m2->p, tab.data(), tab.size(), cudaMemcpyHostToDevice, c->stream));
     g.n_b_dev = dalloc(g.n_b.size() * sizeof(long long), &e);
     MG_CUDA(c, e);
-    MG_CUDA(c, cudaMemcpy(g.n_b_dev->p, g.n_b.data(), g.n_b.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    MG_CUDA(c, cudaMemcpyAsync(g.n_b_dev->p, g.n_b.data(), g.n_b.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
     MG_CUDA(c, cudaStreamSynchronize(c->stream));  // dN, dR, dd freed below
     c->B_max = std::max(c->B_max, g.B);
     c->groups.push_back(std::move(g));
@@ -1217,7 +1217,7 @@ mg_status init_impl(mg_ctx* c, int n_groups, const mg_grid* grids, const double*
       std::vector<double> P0(gg.B + 1, (gg.L * gg.L * gg.L) / double(gg.M));
       if (opt->P0)
         for (int b = 0; b <= gg.B; ++b) P0[b] = opt->P0[b];
-      MG_CUDA(c, cudaMemcpy(ch.P->p, P0.data(), P0.size() * sizeof(double), cudaMemcpyHostToDevice));
+      MG_CUDA(c, cudaMemcpyAsync(ch.P->p, P0.data(), P0.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
       if (opt->start_dispersion > 0.0) {
         disperse_start_kernel<<<1, 256, 0, c->stream>>>(static_cast<double*>(ch.P->p), gg.B + 1,
                                                         opt->start_dispersion, uint32_t(gg.seed & 0xffffffffu),
