@@ -74,6 +74,18 @@ def test_workload_128cubed_holes_fp64_over_100_sweeps():
         assert es <= TOL[64] and ep <= TOL[64], (cp, es, ep)
 
 
+@pytest.mark.parametrize("precision,cluster", [(64, 2), (32, 1), (32, 2)])
+def test_grid_192_draw_for_draw(precision, cluster):
+    """192^3 (192 = 16 x 12: a radix-3 factor in every axis) in each cluster
+    size built for it: FP32 with 1 and 2 CTAs per plane, FP64 with 2."""
+    need_gpu()
+    m = mockgen.make_mock(192, seed=192, n_bins=48)
+    n_chains = 2 if precision == 32 else 1
+    res = compare_run(m, 48, 13, precision, [1, 2], n_chains=n_chains, yz_cluster=cluster)
+    for cp, es, ep in res:
+        assert es <= TOL[precision] and ep <= TOL[precision], (cp, es, ep)
+
+
 @pytest.mark.parametrize("precision,cluster", [(32, 2), (32, 4), (32, 8), (64, 4)])
 def test_workload_256cubed_sampled_chains(precision, cluster):
     """Full-size 256^3 grid in the benchmark's launch form (16 chains in one
