@@ -86,6 +86,30 @@ def test_adjoint_128cubed_fp32_against_central_differences():
             assert abs((gd * u).sum() - fd) <= 2e-3 * abs(fd), ((gd * u).sum(), fd)
 
 
+def test_adjoint_256cubed_cluster_forms_agree():
+    """At 256^3 the FP32 adjoint's y/z pass runs in thread-block clusters, its
+    planes split over 4 (or 2) CTAs that exchange through distributed shared
+    memory, a path the smaller grids above (one CTA per plane) do not take.
+    The adjoint arithmetic they share is checked above; here the two cluster
+    forms must give the same loss and gradients."""
+    need_gpu()
+    w = mockgen.workload(3)
+    m = w.mocks[0]
+    nb, K = m.n_bins, 2
+    wts = mockgen.mode_weights(m.n, 5)
+    V, M = m.L ** 3, m.n ** 3
+    logP = np.log(V / M) + np.random.default_rng(11).uniform(-1.0, 1.0, size=nb + 1)
+    out = {}
+    for c in (4, 2):
+        with gpu_sampler(m, nb, 3, 32, yz_cluster=c) as g:
+            g.sweep(1)
+            out[c] = g.adjoint(0, K, logP, wts)
+    (L4, gl4, gd4), (L2, gl2, gd2) = out[4], out[2]
+    assert np.isfinite(L4) and np.all(np.isfinite(gl4)) and np.all(np.isfinite(gd4))
+    assert abs(L4 - L2) <= 1e-6 * abs(L2), (L4, L2)
+    assert rel_l2(gl4, gl2) <= 1e-5 and rel_l2(gd4, gd2) <= 1e-5, (rel_l2(gl4, gl2), rel_l2(gd4, gd2))
+
+
 def test_autograd_binding_returns_the_adjoint():
     torch = need_gpu()
     from paper_1402_1763_gb300.autograd import gibbs_loss
