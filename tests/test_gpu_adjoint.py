@@ -110,6 +110,27 @@ def test_adjoint_256cubed_cluster_forms_agree():
     assert rel_l2(gl4, gl2) <= 1e-5 and rel_l2(gd4, gd2) <= 1e-5, (rel_l2(gl4, gl2), rel_l2(gd4, gd2))
 
 
+def test_adjoint_128cubed_cluster_matches_single_cta():
+    """At 128^3 the FP32 y/z pass is built both with one CTA per plane (the form
+    checked against central differences above) and with clusters of 2: the
+    adjoint must agree between them."""
+    need_gpu()
+    w5 = mockgen.workload(5)
+    m = w5.mocks[0]
+    nb, K = m.n_bins, 8
+    wts = mockgen.mode_weights(m.n, 5)
+    V, M = m.L ** 3, m.n ** 3
+    logP = np.log(V / M) + np.random.default_rng(9).uniform(-1.0, 1.0, size=nb + 1)
+    out = {}
+    for c in (1, 2):
+        with gpu_sampler(m, nb, 5, 32, yz_cluster=c) as g:
+            g.sweep(2)
+            out[c] = g.adjoint(0, K, logP, wts)
+    (L1, gl1, gd1), (L2, gl2, gd2) = out[1], out[2]
+    assert abs(L1 - L2) <= 1e-6 * abs(L1), (L1, L2)
+    assert rel_l2(gl2, gl1) <= 1e-5 and rel_l2(gd2, gd1) <= 1e-5, (rel_l2(gl2, gl1), rel_l2(gd2, gd1))
+
+
 def test_autograd_binding_returns_the_adjoint():
     torch = need_gpu()
     from paper_1402_1763_gb300.autograd import gibbs_loss
