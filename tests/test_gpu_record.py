@@ -15,7 +15,8 @@ samples (numpy mean and var with ddof = 1 of the same draws):
 * Alternating plain and mixing sweeps (both sweep kinds carry the record).
 * set_s with a sample pending adds the old state first.
 * The sums formed inside the sweep and by the separate pass agree bit for bit
-  (FP64 sums, and the double-float pairs of FP32 samples).
+  (FP64 sums, and the double-float pairs of FP32 samples), also where pass YZ
+  splits its planes over thread-block clusters (128^3, 192^3, 256^3).
 """
 import numpy as np
 import pytest
@@ -117,12 +118,15 @@ def test_set_s_adds_the_pending_sample_first():
     check(st, xs, 1e-12)
 
 
-@pytest.mark.parametrize("precision", [64, 32])
-def test_fused_and_separate_sums_agree_bit_for_bit(precision):
+@pytest.mark.parametrize("n,precision,cluster", [(24, 64, 0), (24, 32, 0), (128, 32, 2), (192, 64, 2),
+                                               (256, 32, 4), (256, 32, 2)])
+def test_fused_and_separate_sums_agree_bit_for_bit(n, precision, cluster):
+    """Also in the cluster forms of pass YZ, whose record mode finds each
+    voxel's sums through the CTA's rank in the cluster."""
     need_gpu()
-    m = mockgen.make_mock(24, seed=76, n_bins=6, sigma_n=0.3)
-    with gpu_sampler(m, 6, 10, precision, record_every=1) as a, \
-            gpu_sampler(m, 6, 10, precision, record_every=1) as b:
+    m = mockgen.make_mock(n, seed=76, n_bins=6, sigma_n=0.3)
+    with gpu_sampler(m, 6, 10, precision, record_every=1, yz_cluster=cluster) as a, \
+            gpu_sampler(m, 6, 10, precision, record_every=1, yz_cluster=cluster) as b:
         for _ in range(6):
             a.sweep(1)
             a.read_stats(0, maps=True)  # every sample added by the separate pass
