@@ -275,6 +275,33 @@ def test_new_data_mid_chain(precision):
                 orc.prob = sampler.make_problem(m.shape, m.L, m.N, m.R, d2, 8)
 
 
+@pytest.mark.parametrize("n,precision,cluster", [(256, 32, 4), (256, 32, 2), (256, 64, 4), (192, 64, 2),
+                                               (128, 32, 2)])
+def test_set_s_read_s_round_trip_in_cluster_forms(n, precision, cluster):
+    """set_s runs pass YZ in its load mode and read_s in its materialise mode;
+    in the cluster forms both go through the exchange between the CTAs of a
+    plane.  A field set and read back is unchanged up to the transforms'
+    rounding (FP64 1e-14, FP32 1e-6 relative L2), the chain then sweeps on,
+    and resuming from a saved state reproduces the same sweeps."""
+    need_gpu()
+    m = mockgen.make_mock(n, seed=53, n_bins=8)
+    s0 = np.random.default_rng(1).standard_normal(m.shape)
+    tol_rt = 1e-14 if precision == 64 else 1e-6
+    with gpu_sampler(m, 8, 5, precision, yz_cluster=cluster) as g:
+        g.set_s(0, s0)
+        assert rel_l2(g.read_s(0), s0) <= tol_rt
+        g.sweep(2)
+        mid_s, mid_p = g.read_s(0), g.read_pk(0)
+        g.sweep(1)
+        s3, p3 = g.read_s(0), g.read_pk(0)
+    with gpu_sampler(m, 8, 5, precision, yz_cluster=cluster) as r:
+        r.set_s(0, mid_s)
+        r.set_pk(0, mid_p)
+        r.sweep_count = 2
+        r.sweep(1)
+        assert rel_l2(r.read_s(0), s3) <= TOL[precision] and rel_l2(r.read_pk(0), p3) <= TOL[precision]
+
+
 def test_workload_128cubed_holes_fp64_over_1000_sweeps():
     """The 128^3 FP64 workload with holes draw for draw over its full 1000
     sweeps, against the oracle's chain stored by
